@@ -1,0 +1,181 @@
+/*
+ * hisq.h -- C ABI of the GB300 HISQ staggered Dslash and its even-odd Krylov solvers.
+ *
+ * The library applies the HISQ Dirac operator of Sec. 5.1 (a one-hop fat-link term X and
+ * a three-hop Naik long-link term W in each of the four directions) on one parity of a
+ * 4D even-odd lattice, and solves A x = b with A = M^+ M = 4m^2 - D_eo D_oe on even
+ * sites (M = 2m + D; Sec. 3.2 "Inverters") by CG, multi-RHS CG and multi-shift CG.
+ *
+ * Conventions shared by every call
+ *   Lattice   dims = {Nx, Ny, Nz, Nt}, each even and >= 4; V = Nx Ny Nz Nt, Vh = V/2.
+ *   Canonical site order (Sec. 4.3): index(x) = floor(lex/2) + Vh ((x+y+z+t) mod 2),
+ *             lex = x + Nx (y + Ny (z + Nz t)); even sites first.
+ *   Links     fat = X, lng = W: complex128 [4][V][3][3], link (mu, x) at index mu*V + index(x),
+ *             row-major 3x3, (re, im) interleaved doubles.  By default WITHOUT staggered
+ *             phases: the library applies the MILC phases eta_0 = 1, eta_1 = (-1)^x,
+ *             eta_2 = (-1)^(x+y), eta_3 = (-1)^(x+y+z) and the antiperiodic time boundary
+ *             of the spinors (Sec. 3), unless hisq_opts.links_phased = 1.
+ *   Vectors   one parity, complex128 [nrhs][Vh][3] in canonical half-index order.
+ *   Streams   `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *             Dslash / normal-operator calls are stream-ordered and asynchronous; solver
+ *             calls synchronise their stream before returning.
+ *   Errors    every int-returning call returns HISQ_OK (0) or one of the codes below and
+ *             records it with a message on the context (hisq_get_last_error,
+ *             hisq_last_error_message).  Nothing throws across the ABI.
+ *   Memory    the library copies the links at hisq_create and owns that copy; all vectors
+ *             passed to calls are owned by the caller and must not alias unless stated.
+ */
+#ifndef HISQ_H
+#define HISQ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+enum hisq_status {
+    HISQ_OK = 0,
+    HISQ_EINVAL = 1,        /* invalid argument (dims, pointers, precision, aliasing, ...)   */
+    HISQ_ENOMEM = 2,        /* device or pinned-host allocation failed                        */
+    HISQ_ECUDA = 3,         /* a CUDA runtime call failed (message holds cudaGetErrorString)  */
+    HISQ_ENOTCONVERGED = 4, /* solver reached maxiter or a non-finite residual; x = last iterate */
+    HISQ_ETIMEOUT = 5,      /* a bounded device-side wait gave up                             */
+    HISQ_EDEVICE = 6,       /* a kernel raised the context's device error flag                */
+    HISQ_ENOTBUILT = 7      /* the requested precision / compression was not built at create  */
+};
+
+/* ------------------------------------------------------------------ precisions */
+enum hisq_prec {
+    HISQ_F64 = 0,  /* IEEE double storage, double arithmetic                                   */
+    HISQ_F64X = 1, /* double-class: each real stored as an unevaluated float pair (hi + lo,
+                      48-bit significand, 8 bytes), float-float arithmetic on the FP32 pipes  */
+    HISQ_F32 = 2,  /* float storage and arithmetic                                             */
+    HISQ_F16 = 3,  /* half storage (spinors: one float scale per site; links: one float scale
+                      per link type), float arithmetic                                         */
+    HISQ_BF16 = 4, /* as HISQ_F16 with bfloat16 storage                                        */
+    HISQ_NPREC = 5
+};
+
+/* ------------------------------------------------------------------ context */
+typedef struct hisq_ctx hisq_ctx;
+
+typedef struct {
+    int links_on_device;       /* 1: fat/lng are device pointers; 0: host pointers              */
+    int links_phased;          /* 1: links already contain eta_mu(x) and the time boundary sign
+                                  (on the link whose forward hop wraps); 18-real only           */
+    unsigned prec_mask;        /* bit (1u << HISQ_xxx) per storage precision to build;
+                                  0 = F64 | F64X | F32 | F16                                    */
+    int compression[HISQ_NPREC]; /* 18 (default, also 0) or 12 real numbers per link, per
+                                  precision.  12 stores two rows of L/c with c a real constant
+                                  per link type such that L/c is in SU(3) (checked at create,
+                                  HISQ_EINVAL otherwise) and rebuilds the third row from them  */
+    int device;                /* CUDA device ordinal                                            */
+} hisq_opts;
+
+/* Fill `opts` with the defaults (host links, unphased, F64|F64X|F32|F16, 18 reals, device 0). */
+void hisq_opts_default(hisq_opts *opts);
+
+/* Create a context for one lattice: validates dims (each even, >= 4), copies the links to
+ * the device and prepares one internal link store per requested precision (phases folded,
+ * compressed, quantised; Sec. 5.1 and the commented compression remark beside it).
+ * On error *ctx is NULL.  Links are read, never retained. */
+int hisq_create(hisq_ctx **ctx, const int dims[4], const double *fat, const double *lng,
+                const hisq_opts *opts);
+
+/* Release all device memory of the context.  NULL is accepted. */
+void hisq_destroy(hisq_ctx *ctx);
+
+/* Last status recorded on the context (0 if none) and its message (never NULL). */
+int hisq_get_last_error(const hisq_ctx *ctx);
+const char *hisq_last_error_message(const hisq_ctx *ctx);
+const char *hisq_strerror(int status);
+
+/* Geometry queries: half volume and the padded half volume used by internal fields. */
+long hisq_half_volume(const hisq_ctx *ctx);
+
+/* ------------------------------------------------------------------ internal-layout fields */
+/* A field holds nrhs half-lattice vectors in a precision's internal layout (site-major,
+ * 16-byte aligned).  It exists so that reduced-precision operators can be applied and
+ * timed without per-call conversions. */
+typedef struct hisq_field hisq_field;
+
+int hisq_field_create(hisq_ctx *ctx, int prec, int nrhs, hisq_field **f);
+void hisq_field_destroy(hisq_field *f);
+/* canonical complex128 [nrhs][Vh][3] (device pointer) <-> internal; stream-ordered */
+int hisq_field_import(hisq_field *f, const double *src, void *stream);
+int hisq_field_export(const hisq_field *f, double *dst, void *stream);
+/* bytes of device memory held by the field */
+size_t hisq_field_bytes(const hisq_field *f);
+
+/* ------------------------------------------------------------------ operators */
+/* out = D_{p,1-p} in (Sec. 5.1 stencil; p = out_parity).  `in` holds parity 1-p, `out`
+ * receives parity p, both canonical complex128 [nrhs][Vh][3] DEVICE buffers that must not
+ * overlap.  `prec` selects the arithmetic/storage of the applied operator; for prec !=
+ * HISQ_F64 the vectors are converted to that precision on the way in and back to double on
+ * the way out.  Returns HISQ_ENOTBUILT if the context lacks that precision. */
+int hisq_dslash(hisq_ctx *ctx, int out_parity, const double *in, double *out, int nrhs, int prec,
+                void *stream);
+
+/* out = D_{p,1-p} in on internal fields of the same precision and nrhs (no conversions). */
+int hisq_dslash_field(hisq_ctx *ctx, int out_parity, const hisq_field *in, hisq_field *out,
+                      void *stream);
+
+/* out = (4 m^2 - D_eo D_oe) in on even sites (A = M^+ M, Sec. 3.2 applyMdaggM);
+ * canonical complex128 [nrhs][Vh][3] device buffers, no overlap. */
+int hisq_mdagm(hisq_ctx *ctx, double m, const double *in, double *out, int nrhs, int prec,
+               void *stream);
+
+/* ------------------------------------------------------------------ solvers */
+typedef struct {
+    double tol;            /* target |b - A x| / |b| (recomputed in FP64), e.g. 1e-10       */
+    int maxiter;           /* iteration cap (sloppy iterations)                              */
+    int prec_sloppy;       /* precision of the iterated operator and vectors: HISQ_F64 gives
+                              plain double CG; F64X/F32/F16/BF16 give mixed precision       */
+    int prec_precise;      /* operator for reliable updates and the final residual: HISQ_F64
+                              or HISQ_F64X                                                   */
+    int reliable_interval; /* sloppy iterations between reliable updates (default 100)       */
+    double reliable_delta; /* also update when |r| < delta * |r| at the last update (0.1)    */
+    int zero_guess;        /* 1: start from x = 0; 0: x holds the initial guess              */
+    int host_buffers;      /* 1: b and x are host pointers (copied inside the call)          */
+    int check_interval;    /* iterations between host-side convergence checks (default 50)   */
+    int use_graph;         /* 1: replay iteration blocks as a captured CUDA graph            */
+    int profile;           /* 1: time every sloppy Dslash launch with CUDA events            */
+    void *stream;          /* cudaStream_t (NULL = legacy default stream)                    */
+} hisq_solve_opts;
+
+typedef struct {
+    int iterations;          /* sloppy iterations (max over right-hand sides / shifts)       */
+    int reliable_updates;    /* FP64 residual recomputations                                  */
+    double true_residual;    /* max over rhs / shifts of |b - A x| / |b|, recomputed          */
+    double iterated_residual;/* iterated residual estimate at exit                            */
+    double seconds;          /* wall time of the call                                         */
+    long dslash_calls;       /* Dslash applications (all precisions)                          */
+    double dslash_ms;        /* summed event time of the timed sloppy Dslash launches         */
+    long dslash_timed;       /* number of timed launches (profile = 1)                        */
+    double bytes_moved;      /* algorithmic bytes of all kernels (links + vectors)            */
+} hisq_stats;
+
+void hisq_solve_opts_default(hisq_solve_opts *o);
+
+/* CG on A x_k = b_k for k < nrhs (Sec. 3.2; nrhs > 1 is the multi-RHS variant).
+ * b, x: canonical complex128 [nrhs][Vh][3], device buffers unless opts->host_buffers.
+ * Returns HISQ_OK once every true residual <= tol, HISQ_ENOTCONVERGED otherwise (x = the
+ * last iterate, stats filled).  `residuals` (may be NULL) receives nrhs true residuals. */
+int hisq_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs,
+            const hisq_solve_opts *opts, hisq_stats *stats, double *residuals);
+
+/* Multi-shift CG: (A + sigma_s) x_s = b for s < nshift, one operator application per
+ * iteration on the smallest shift (Sec. 3.2 and its reference to Jegerlehner).
+ * sigma_s >= 0 in any order; x[s] are caller-owned [Vh][3] buffers; tol[s] per shift (NULL:
+ * opts->tol).  In a reduced sloppy precision every shift is finished by mixed-precision CG
+ * from its multi-shift iterate.  `residuals` (may be NULL) receives nshift true residuals. */
+int hisq_multishift_cg(hisq_ctx *ctx, double m, int nshift, const double *sigma,
+                       const double *b, double *const *x, const double *tol,
+                       const hisq_solve_opts *opts, hisq_stats *stats, double *residuals);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HISQ_H */

@@ -1,0 +1,246 @@
+// blas.cuh -- fused vector kernels of the Krylov solvers (one pass over each vector).
+//
+// Vectors are internal-layout fields (VecRef: base + bytes between right-hand sides);
+// grid.y runs over right-hand sides, grid.x is a fixed number of blocks looping over
+// sites, so every reduction has a fixed partial count and a fixed summation order.
+// Reductions accumulate per thread in the compute type of the field, per block and grid
+// in FP64.  Kernels skip right-hand sides whose coefficients are zero (converged).
+#pragma once
+
+#include "arith.cuh"
+#include "reduce.cuh"
+
+namespace hisq {
+
+constexpr int kVecBlock = 256;
+
+struct VecRef {
+    char *p;
+    size_t rb; // bytes between right-hand sides
+    __device__ __forceinline__ char *rhs(int r) const { return p + (size_t)r * rb; }
+};
+
+// ---------------------------------------------------------------- element operations
+// y += a x ; y = x + b y ; |x|^2 ; conversions via double components
+template <int P> struct Blas {
+    using T = Prec<P>;
+    using Vec = typename T::Vec;
+    __device__ static void axpy(Vec &y, double a, const Vec &x)
+    {
+        const typename T::Real ar = (typename T::Real)a;
+#pragma unroll
+        for (int i = 0; i < 6; i++) y.v[i] = ar * x.v[i] + y.v[i];
+    }
+    __device__ static void xpay(Vec &y, const Vec &x, double b)
+    {
+        const typename T::Real br = (typename T::Real)b;
+#pragma unroll
+        for (int i = 0; i < 6; i++) y.v[i] = br * y.v[i] + x.v[i];
+    }
+    __device__ static double norm2(const Vec &x)
+    {
+        typename T::Real s = 0;
+#pragma unroll
+        for (int i = 0; i < 6; i++) s += x.v[i] * x.v[i];
+        return (double)s;
+    }
+    __device__ static void store(char *base, uint32_t s, const Vec &x)
+    {
+        typename T::Acc a;
+#pragma unroll
+        for (int i = 0; i < 6; i++) a.v[i] = x.v[i];
+        T::store(base, s, a);
+    }
+    __device__ static double get(const Vec &x, int i) { return (double)x.v[i]; }
+    __device__ static void set(Vec &x, int i, double d) { x.v[i] = (typename T::Real)d; }
+};
+
+// float pairs: compensated updates on the FP32 pipes
+template <> struct Blas<HISQ_F64X> {
+    using T = Prec<HISQ_F64X>;
+    using Vec = T::Vec;
+    __device__ static void axpy(Vec &y, double a, const Vec &x)
+    {
+        const float ah = (float)a, al = (float)(a - (double)ah);
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            DAcc c = {y.h[i], y.l[i]};
+            dd_mac(c, ah, al, x.h[i], x.l[i]);
+            const DD d = dd_norm(c);
+            y.h[i] = d.h;
+            y.l[i] = d.l;
+        }
+    }
+    __device__ static void xpay(Vec &y, const Vec &x, double b)
+    {
+        const float bh = (float)b, bl = (float)(b - (double)bh);
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            DAcc c = {x.h[i], x.l[i]};
+            dd_mac(c, bh, bl, y.h[i], y.l[i]);
+            const DD d = dd_norm(c);
+            y.h[i] = d.h;
+            y.l[i] = d.l;
+        }
+    }
+    __device__ static double norm2(const Vec &x)
+    {
+        DAcc c = {0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 6; i++) dd_mac(c, x.h[i], x.l[i], x.h[i], x.l[i]);
+        return (double)c.h + (double)c.e;
+    }
+    __device__ static void store(char *base, uint32_t s, const Vec &x)
+    {
+        float4 *q = reinterpret_cast<float4 *>(base + (size_t)s * T::SB);
+        q[0] = make_float4(x.h[0], x.h[1], x.h[2], x.h[3]);
+        q[1] = make_float4(x.h[4], x.h[5], x.l[0], x.l[1]);
+        q[2] = make_float4(x.l[2], x.l[3], x.l[4], x.l[5]);
+    }
+    __device__ static double get(const Vec &x, int i) { return (double)x.h[i] + (double)x.l[i]; }
+    __device__ static void set(Vec &x, int i, double d)
+    {
+        const float h = (float)d;
+        x.h[i] = h;
+        x.l[i] = (float)(d - (double)h);
+    }
+};
+
+template <int P>
+__device__ __forceinline__ void vload(const char *base, uint32_t s, typename Prec<P>::Vec &v)
+{
+    Prec<P>::load(base, s, v);
+}
+
+// ---------------------------------------------------------------- kernels
+// r -= alpha Ap ; |r|^2 reduced with FIN_RR (beta, convergence flags)
+template <int PS>
+__global__ void __launch_bounds__(kVecBlock) k_update_r(VecRef r, VecRef Ap, uint32_t Vh, Reduce red)
+{
+    using B = Blas<PS>;
+    const int rhs = blockIdx.y;
+    const double alpha = red.sc[rhs].alpha;
+    double acc = 0.0;
+    if (alpha != 0.0) {
+        char *rp = r.rhs(rhs);
+        const char *ap = Ap.rhs(rhs);
+        for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+            typename B::Vec rv, av;
+            vload<PS>(rp, s, rv);
+            vload<PS>(ap, s, av);
+            B::axpy(rv, -alpha, av);
+            B::store(rp, s, rv);
+            acc += B::norm2(rv);
+        }
+    }
+    double mine[1] = {block_sum(acc)};
+    grid_reduce<1>(red, mine, 1, rhs, gridDim.y, blockIdx.x);
+}
+
+// mode 0: x += alpha p, p = r + beta p;  mode 1: x += alpha p;  mode 2: p = r + beta p
+template <int PS, int PX>
+__global__ void __launch_bounds__(kVecBlock) k_update_xp(VecRef x, VecRef p, VecRef r, uint32_t Vh, const Scalars *sc,
+                                                         int mode)
+{
+    using BS = Blas<PS>;
+    using BX = Blas<PX>;
+    const int rhs = blockIdx.y;
+    const double alpha = sc[rhs].alpha, beta = sc[rhs].beta;
+    const bool do_x = mode != 2 && alpha != 0.0;
+    const bool do_p = mode != 1 && sc[rhs].active;
+    if (!do_x && !do_p) return;
+    char *xp = x.rhs(rhs), *pp = p.rhs(rhs);
+    const char *rp = r.rhs(rhs);
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+        typename BS::Vec pv;
+        vload<PS>(pp, s, pv);
+        if (do_x) {
+            typename BX::Vec xv, pc;
+            vload<PX>(xp, s, xv);
+#pragma unroll
+            for (int i = 0; i < 6; i++) BX::set(pc, i, BS::get(pv, i));
+            BX::axpy(xv, alpha, pc);
+            BX::store(xp, s, xv);
+        }
+        if (do_p) {
+            typename BS::Vec rv;
+            vload<PS>(rp, s, rv);
+            BS::xpay(pv, rv, beta);
+            BS::store(pp, s, pv);
+        }
+    }
+}
+
+// out (PB) = in (PA), element-wise through double components
+template <int PA, int PB>
+__global__ void __launch_bounds__(kVecBlock) k_convert(VecRef in, VecRef out, uint32_t Vh)
+{
+    const int rhs = blockIdx.y;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+        typename Blas<PA>::Vec a;
+        typename Blas<PB>::Vec b;
+        vload<PA>(in.rhs(rhs), s, a);
+#pragma unroll
+        for (int i = 0; i < 6; i++) Blas<PB>::set(b, i, Blas<PA>::get(a, i));
+        Blas<PB>::store(out.rhs(rhs), s, b);
+    }
+}
+
+// x_hi (F64) += x_lo (PX); x_lo = 0
+template <int PX>
+__global__ void __launch_bounds__(kVecBlock) k_accum_hi(VecRef xhi, VecRef xlo, uint32_t Vh)
+{
+    const int rhs = blockIdx.y;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+        typename Blas<PX>::Vec l, z;
+        typename Blas<HISQ_F64>::Vec h;
+        vload<PX>(xlo.rhs(rhs), s, l);
+        vload<HISQ_F64>(xhi.rhs(rhs), s, h);
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            h.v[i] += Blas<PX>::get(l, i);
+            Blas<PX>::set(z, i, 0.0);
+        }
+        Blas<HISQ_F64>::store(xhi.rhs(rhs), s, h);
+        Blas<PX>::store(xlo.rhs(rhs), s, z);
+    }
+}
+
+// r (F64) = b (F64) - Ax (PA); |r|^2 reduced (FIN_STORE -> Scalars.last)
+template <int PA>
+__global__ void __launch_bounds__(kVecBlock) k_residual(VecRef b, VecRef Ax, VecRef r, uint32_t Vh, Reduce red)
+{
+    const int rhs = blockIdx.y;
+    double acc = 0.0;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+        typename Blas<HISQ_F64>::Vec bv, rv;
+        typename Blas<PA>::Vec av;
+        vload<HISQ_F64>(b.rhs(rhs), s, bv);
+        vload<PA>(Ax.rhs(rhs), s, av);
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            rv.v[i] = bv.v[i] - Blas<PA>::get(av, i);
+            acc = fma(rv.v[i], rv.v[i], acc);
+        }
+        Blas<HISQ_F64>::store(r.rhs(rhs), s, rv);
+    }
+    double mine[1] = {block_sum(acc)};
+    grid_reduce<1>(red, mine, 1, rhs, gridDim.y, blockIdx.x);
+}
+
+// |x|^2 (F64) reduced with FIN_STORE
+__global__ void __launch_bounds__(kVecBlock) k_norm_f64(VecRef x, uint32_t Vh, Reduce red)
+{
+    const int rhs = blockIdx.y;
+    double acc = 0.0;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+        typename Blas<HISQ_F64>::Vec v;
+        vload<HISQ_F64>(x.rhs(rhs), s, v);
+#pragma unroll
+        for (int i = 0; i < 6; i++) acc = fma(v.v[i], v.v[i], acc);
+    }
+    double mine[1] = {block_sum(acc)};
+    grid_reduce<1>(red, mine, 1, rhs, gridDim.y, blockIdx.x);
+}
+
+}  // namespace hisq

@@ -1,0 +1,490 @@
+// cg.cu -- conjugate gradient on A = 4m^2 - D_eo D_oe (Sec. 3.2), single and multi-RHS,
+// plain FP64 or mixed precision with reliable updates.
+//
+// Iteration (all scalars stay on the device; one grid reduction per inner product):
+//   t  = D_oe p                          sloppy Dslash
+//   Ap = m4 p - D_eo t, <p,Ap> -> alpha  sloppy Dslash + fused epilogue/reduction
+//   r -= alpha Ap, |r|^2 -> beta         fused update/reduction
+//   x_lo += alpha p, p = r + beta p      fused update
+// The host launches blocks of `check_interval` iterations (optionally one captured CUDA
+// graph per block) and reads the scalars only between blocks.  Reliable update (mixed
+// precision; the scheme the paper's mixed-precision citation describes):
+//   x_hi += x_lo, x_lo = 0, r_hi = b - A_precise x_hi (FP64 or float-pair operator),
+//   r = sloppy(r_hi), beta = |r_hi|^2 / |r_old|^2, p = r + beta p;
+// triggered every `reliable_interval` iterations, when the sloppy residual fell below
+// delta times the last true one, or when it reached the target.  The solve ends when
+// every recomputed residual |b - A x| / |b| <= tol.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "blas.cuh"
+#include "dslash.cuh"
+#include "solver.cuh"
+
+namespace hisq {
+
+int apply_mdagm(hisq_ctx *ctx, int prec, double m, const void *in, void *tmp, void *out, int nrhs, size_t rhs_bytes,
+                cudaStream_t st, const Reduce *red);
+
+// ---------------------------------------------------------------- scalar bookkeeping
+enum { SC_INIT_BB = 0, SC_INIT_R = 1, SC_RU = 2 };
+
+__global__ void k_scalars(Scalars *sc, int n, int mode, double tol2, double delta2)
+{
+    const int r = threadIdx.x;
+    if (r >= n) return;
+    Scalars &S = sc[r];
+    switch (mode) {
+    case SC_INIT_BB:
+        S.bb = S.last;
+        S.stop = tol2 * S.last;
+        S.delta2 = delta2;
+        S.iters = 0;
+        S.bad = 0;
+        break;
+    case SC_INIT_R:
+        S.rr = S.last;
+        S.rr_ref = S.last;
+        S.alpha = S.beta = 0.0;
+        S.flag = 0;
+        S.active = (S.last > S.stop) && isfinite(S.last);
+        if (!isfinite(S.last)) S.bad = 1;
+        break;
+    default: { // reliable update: S.last = |b - A x_hi|^2
+        const double rt = S.last;
+        if (!isfinite(rt)) {
+            S.bad = 1;
+            S.active = 0;
+            S.beta = 0.0;
+        } else if (rt <= S.stop) {
+            S.active = 0;
+            S.beta = 0.0;
+        } else {
+            // continuing: beta = |r_true|^2 / |r_old|^2 with |r_old|^2 = rr / beta
+            S.beta = (S.active && S.rr > 0.0) ? S.beta * rt / S.rr : 0.0;
+            S.active = 1;
+        }
+        S.rr = rt;
+        S.rr_ref = rt;
+        S.flag = 0;
+        break;
+    }
+    }
+}
+
+static double wall()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static int accum_prec(int ps) { return (ps == HISQ_F64 || ps == HISQ_F64X) ? ps : HISQ_F32; }
+
+// ---------------------------------------------------------------- typed launches
+template <int PS, int PX>
+struct Typed {
+    static void update_r(SolverWork &w, cudaStream_t st)
+    {
+        k_update_r<PS><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.r, w.rbS}, VecRef{w.Ap, w.rbS}, w.Vh,
+                                                                       w.red(FIN_RR, w.nblk_vec));
+    }
+    static void update_xp(SolverWork &w, int mode, cudaStream_t st)
+    {
+        k_update_xp<PS, PX><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(
+            VecRef{w.xlo, w.rbX}, VecRef{w.p, w.rbS}, VecRef{w.r, w.rbS}, w.Vh, w.sc, mode);
+    }
+    static void accum_hi(SolverWork &w, cudaStream_t st)
+    {
+        k_accum_hi<PX><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.x64, w.rb64}, VecRef{w.xlo, w.rbX}, w.Vh);
+    }
+    static void from_hi(SolverWork &w, char *dst, cudaStream_t st)
+    {
+        k_convert<HISQ_F64, PS><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.rhi, w.rb64}, VecRef{dst, w.rbS},
+                                                                               w.Vh);
+    }
+};
+
+template <class F>
+static void dispatch(int ps, F &&f)
+{
+    switch (ps) {
+    case HISQ_F64: f(Typed<HISQ_F64, HISQ_F64>{}); break;
+    case HISQ_F64X: f(Typed<HISQ_F64X, HISQ_F64X>{}); break;
+    case HISQ_F32: f(Typed<HISQ_F32, HISQ_F32>{}); break;
+    case HISQ_F16: f(Typed<HISQ_F16, HISQ_F32>{}); break;
+    default: f(Typed<HISQ_BF16, HISQ_F32>{}); break;
+    }
+}
+
+// ---------------------------------------------------------------- workspace
+void SolverWork::release()
+{
+    for (void *q : allocs) cudaFree(q);
+    allocs.clear();
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    for (auto e : prof) cudaEventDestroy(e);
+    prof.clear();
+    if (h_sc) cudaFreeHost(h_sc);
+    h_sc = nullptr;
+    if (st) cudaStreamDestroy(st);
+    st = nullptr;
+    if (ev) cudaEventDestroy(ev);
+    ev = nullptr;
+}
+
+int SolverWork::alloc(hisq_ctx *ctx, char **ptr, size_t bytes)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "solver workspace");
+    cudaMemset(q, 0, bytes ? bytes : 16);
+    allocs.push_back(q);
+    *ptr = static_cast<char *>(q);
+    return HISQ_OK;
+}
+
+Reduce SolverWork::red(int op, int nblocks_per_value, int ntotal) const
+{
+    Reduce R;
+    R.partials = partials;
+    R.counter = counter;
+    R.sc = sc;
+    R.op = op;
+    R.nblocks = nblocks_per_value;
+    R.ntotal = ntotal ? ntotal : nblocks_per_value * nrhs;
+    return R;
+}
+
+int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out)
+{
+    SolverWork *&w = ctx->solver;
+    if (w && w->nrhs == nrhs && w->ps == ps && w->pp == pp) {
+        *out = w;
+        return HISQ_OK;
+    }
+    if (w) {
+        cudaDeviceSynchronize();
+        w->release();
+        delete w;
+        w = nullptr;
+    }
+    w = new SolverWork();
+    SolverWork &W = *w;
+    W.nrhs = nrhs;
+    W.ps = ps;
+    W.px = accum_prec(ps);
+    W.pp = pp;
+    W.Vh = ctx->g.Vh;
+    W.rbS = (size_t)ctx->g.VhPad * spinor_bytes(ps);
+    W.rbX = (size_t)ctx->g.VhPad * spinor_bytes(W.px);
+    W.rb64 = (size_t)ctx->g.Vh * 48;
+    W.rbP = (size_t)ctx->g.VhPad * 48;
+    W.nblk_vec = (int)std::min<long>((W.Vh + kVecBlock - 1) / kVecBlock, 4L * ctx->sm_count);
+    W.nblk_dslash = (int)((W.Vh + kDslashBlock - 1) / kDslashBlock);
+    int rc = HISQ_OK;
+    auto A = [&](char **p, size_t b) { if (rc == HISQ_OK) rc = W.alloc(ctx, p, b); };
+    A(&W.r, W.rbS * nrhs);
+    A(&W.p, W.rbS * nrhs);
+    A(&W.Ap, W.rbS * nrhs);
+    A(&W.t, W.rbS * nrhs);
+    A(&W.xlo, W.rbX * nrhs);
+    A(&W.b64, W.rb64 * nrhs);
+    A(&W.x64, W.rb64 * nrhs);
+    A(&W.rhi, W.rb64 * nrhs);
+    A(&W.Axhi, W.rb64 * nrhs);
+    A(&W.thi, W.rb64 * nrhs);
+    if (pp == HISQ_F64X) {
+        A(&W.xx, W.rbP * nrhs);
+        A(&W.tx, W.rbP * nrhs);
+        A(&W.Axx, W.rbP * nrhs);
+    }
+    char *tmp = nullptr;
+    A(&tmp, sizeof(Scalars) * (nrhs + 64));
+    W.sc = reinterpret_cast<Scalars *>(tmp);
+    A(&tmp, sizeof(double) * (size_t)(nrhs + 64) * std::max(W.nblk_vec, W.nblk_dslash));
+    W.partials = reinterpret_cast<double *>(tmp);
+    A(&tmp, 64);
+    W.counter = reinterpret_cast<unsigned *>(tmp);
+    if (rc) return rc;
+    if (cudaMallocHost(&W.h_sc, sizeof(Scalars) * (nrhs + 64)) != cudaSuccess) return set_error(ctx, HISQ_ENOMEM, "pinned scalars");
+    if (cudaStreamCreateWithFlags(&W.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&W.ev, cudaEventDisableTiming) != cudaSuccess)
+        return set_error(ctx, HISQ_ECUDA, "solver stream");
+    *out = w;
+    return HISQ_OK;
+}
+
+void release_work(hisq_ctx *ctx)
+{
+    if (ctx->solver) {
+        ctx->solver->release();
+        delete ctx->solver;
+        ctx->solver = nullptr;
+    }
+}
+
+// ---------------------------------------------------------------- pieces of the iteration
+static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, cudaEvent_t *evs)
+{
+    const LinkStore &L = ctx->links[w.ps];
+    const int nr = pick_inner(w.ps, w.nrhs);
+    DslashArgs a = make_dslash_args(ctx, w.ps, 1, w.p, w.t, w.nrhs, w.rbS);
+    a.skip = w.sc;
+    if (evs) cudaEventRecordWithFlags(evs[0], st, cudaEventRecordExternal);
+    cudaError_t e = dslash_launch(w.ps, 0, a, L.nreal, nr, st);
+    if (evs) cudaEventRecordWithFlags(evs[1], st, cudaEventRecordExternal);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "sloppy dslash");
+    DslashArgs b = make_dslash_args(ctx, w.ps, 0, w.t, w.Ap, w.nrhs, w.rbS);
+    b.skip = w.sc;
+    b.pv = w.p;
+    b.m4 = 4.0 * m * m;
+    const int gx = w.nblk_dslash;
+    b.red = w.red(FIN_ALPHA, gx, gx * (w.nrhs / nr));
+    if (evs) cudaEventRecordWithFlags(evs[2], st, cudaEventRecordExternal);
+    e = dslash_launch(w.ps, 1, b, L.nreal, nr, st);
+    if (evs) cudaEventRecordWithFlags(evs[3], st, cudaEventRecordExternal);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "sloppy dslash + epilogue");
+    return HISQ_OK;
+}
+
+static int launch_block(hisq_ctx *ctx, SolverWork &w, double m, int n, cudaStream_t st, bool prof)
+{
+    for (int i = 0; i < n; i++) {
+        int rc = sloppy_dslash_pair(ctx, w, m, st, prof ? &w.prof[4 * i] : nullptr);
+        if (rc) return rc;
+        dispatch(w.ps, [&](auto T) {
+            decltype(T)::update_r(w, st);
+            decltype(T)::update_xp(w, i == n - 1 ? 1 : 0, st);
+        });
+    }
+    HISQ_CUDA(ctx, cudaGetLastError());
+    return HISQ_OK;
+}
+
+// r_hi = b - A_precise x_hi ; |r_hi|^2 -> Scalars.last
+int precise_residual(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st)
+{
+    int rc;
+    const dim3 g(w.nblk_vec, w.nrhs);
+    if (w.pp == HISQ_F64) {
+        if ((rc = apply_mdagm(ctx, HISQ_F64, m, w.x64, w.thi, w.Axhi, w.nrhs, w.rb64, st, nullptr))) return rc;
+        k_residual<HISQ_F64><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axhi, w.rb64}, VecRef{w.rhi, w.rb64},
+                                                     w.Vh, w.red(FIN_STORE, w.nblk_vec));
+    } else {
+        k_convert<HISQ_F64, HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.x64, w.rb64}, VecRef{w.xx, w.rbP}, w.Vh);
+        if ((rc = apply_mdagm(ctx, HISQ_F64X, m, w.xx, w.tx, w.Axx, w.nrhs, w.rbP, st, nullptr))) return rc;
+        k_residual<HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axx, w.rbP}, VecRef{w.rhi, w.rb64},
+                                                      w.Vh, w.red(FIN_STORE, w.nblk_vec));
+    }
+    HISQ_CUDA(ctx, cudaGetLastError());
+    return HISQ_OK;
+}
+
+static int read_scalars(hisq_ctx *ctx, SolverWork &w, cudaStream_t st)
+{
+    HISQ_CUDA(ctx, cudaMemcpyAsync(w.h_sc, w.sc, sizeof(Scalars) * w.nrhs, cudaMemcpyDeviceToHost, st));
+    HISQ_CUDA(ctx, cudaStreamSynchronize(st));
+    return HISQ_OK;
+}
+
+// ---------------------------------------------------------------- the solve
+int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const hisq_solve_opts &o, hisq_stats *stats,
+           double *residuals)
+{
+    const double t0 = wall();
+    int ps = o.prec_sloppy, pp = o.prec_precise;
+    if (ps < 0 || ps >= HISQ_NPREC || (pp != HISQ_F64 && pp != HISQ_F64X))
+        return set_error(ctx, HISQ_EINVAL, "hisq_cg: bad precision");
+    if (!ctx->links[ps].built || !ctx->links[pp].built)
+        return set_error(ctx, HISQ_ENOTBUILT, "hisq_cg: precision not built");
+    SolverWork *wp = nullptr;
+    int rc = get_work(ctx, nrhs, ps, pp, &wp);
+    if (rc) return rc;
+    SolverWork &w = *wp;
+    cudaStream_t ust = (cudaStream_t)o.stream, st = w.st;
+    HISQ_CUDA(ctx, cudaEventRecord(w.ev, ust));
+    HISQ_CUDA(ctx, cudaStreamWaitEvent(st, w.ev, 0));
+    const size_t vb = (size_t)nrhs * w.rb64;
+    const cudaMemcpyKind k_in = o.host_buffers ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    HISQ_CUDA(ctx, cudaMemcpyAsync(w.b64, b, vb, k_in, st));
+    if (o.zero_guess) HISQ_CUDA(ctx, cudaMemsetAsync(w.x64, 0, vb, st));
+    else HISQ_CUDA(ctx, cudaMemcpyAsync(w.x64, x, vb, k_in, st));
+    HISQ_CUDA(ctx, cudaMemsetAsync(w.xlo, 0, w.rbX * nrhs, st));
+    const dim3 g(w.nblk_vec, nrhs);
+    const double tol2 = o.tol * o.tol;
+    const double delta2 = o.reliable_delta * o.reliable_delta;
+    // |b|^2
+    k_norm_f64<<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, w.Vh, w.red(FIN_STORE, w.nblk_vec));
+    k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_INIT_BB, tol2, ps == HISQ_F64 ? 0.0 : delta2);
+    // r_hi = b - A x0
+    if (o.zero_guess) {
+        HISQ_CUDA(ctx, cudaMemcpyAsync(w.rhi, w.b64, vb, cudaMemcpyDeviceToDevice, st));
+        k_norm_f64<<<g, kVecBlock, 0, st>>>(VecRef{w.rhi, w.rb64}, w.Vh, w.red(FIN_STORE, w.nblk_vec));
+    } else if ((rc = precise_residual(ctx, w, m, st))) {
+        return rc;
+    }
+    k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_INIT_R, tol2, delta2);
+    dispatch(ps, [&](auto T) {
+        decltype(T)::from_hi(w, w.r, st);
+        decltype(T)::from_hi(w, w.p, st);
+    });
+    HISQ_CUDA(ctx, cudaGetLastError());
+
+    const int ci = std::max(1, o.check_interval);
+    const int interval = ps == HISQ_F64 ? (1 << 30) : std::max(1, o.reliable_interval);
+    const bool prof = o.profile != 0;
+    if (prof && (int)w.prof.size() < 4 * ci) {
+        for (int i = (int)w.prof.size(); i < 4 * ci; i++) {
+            cudaEvent_t e;
+            HISQ_CUDA(ctx, cudaEventCreate(&e));
+            w.prof.push_back(e);
+        }
+        if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
+    }
+    int total = 0, since_ru = 0, nru = 0, prev_iters = 0;
+    long dcalls = 0;
+    double dms = 0.0;
+    long dtimed = 0;
+    bool done = false;
+    rc = read_scalars(ctx, w, st);
+    if (rc) return rc;
+    {
+        bool any = false;
+        for (int r = 0; r < nrhs; r++) any |= w.h_sc[r].active != 0;
+        done = !any;
+    }
+    while (!done) {
+        const int n = std::min(ci, o.maxiter - total);
+        if (n <= 0) break;
+        const bool use_graph = o.use_graph && n == ci;
+        if (use_graph) {
+            if (!w.graph || w.graph_n != n || w.graph_m != m || w.graph_prof != prof) {
+                if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
+                cudaGraph_t gr;
+                HISQ_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                rc = launch_block(ctx, w, m, n, st, prof);
+                cudaError_t e = cudaStreamEndCapture(st, &gr);
+                if (rc) return rc;
+                if (e != cudaSuccess) return cuda_error(ctx, e, "graph capture");
+                e = cudaGraphInstantiate(&w.graph, gr, 0);
+                cudaGraphDestroy(gr);
+                if (e != cudaSuccess) return cuda_error(ctx, e, "graph instantiate");
+                w.graph_n = n;
+                w.graph_m = m;
+                w.graph_prof = prof;
+            }
+            HISQ_CUDA(ctx, cudaGraphLaunch(w.graph, st));
+        } else if ((rc = launch_block(ctx, w, m, n, st, prof))) {
+            return rc;
+        }
+        total += n;
+        since_ru += n;
+        if ((rc = read_scalars(ctx, w, st))) return rc;
+        int it = 0;
+        bool any_active = false, any_flag = false;
+        for (int r = 0; r < nrhs; r++) {
+            it = std::max(it, w.h_sc[r].iters);
+            any_active |= w.h_sc[r].active != 0;
+            any_flag |= w.h_sc[r].flag != 0;
+        }
+        const int ran = it - prev_iters; // iterations that did work in this block
+        prev_iters = it;
+        dcalls += 2L * ran;
+        if (prof) {
+            for (int i = 0; i < ran && i < n; i++)
+                for (int j = 0; j < 2; j++) {
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, w.prof[4 * i + 2 * j], w.prof[4 * i + 2 * j + 1]) == cudaSuccess) {
+                        dms += ms;
+                        dtimed++;
+                    }
+                }
+        }
+        const bool last = total >= o.maxiter;
+        if (any_flag || since_ru >= interval || !any_active || last) {
+            dispatch(ps, [&](auto T) { decltype(T)::accum_hi(w, st); });
+            if ((rc = precise_residual(ctx, w, m, st))) return rc;
+            k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_RU, tol2, delta2);
+            dispatch(ps, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
+            nru++;
+            since_ru = 0;
+            if ((rc = read_scalars(ctx, w, st))) return rc;
+            bool any = false;
+            for (int r = 0; r < nrhs; r++) any |= w.h_sc[r].active != 0;
+            if (!any || last) break;
+        }
+        dispatch(ps, [&](auto T) { decltype(T)::update_xp(w, 2, st); });
+    }
+    // every exit from the loop follows a reliable update (or no iteration at all), so
+    // x_hi holds the whole solution and Scalars.rr its recomputed residual
+    HISQ_CUDA(ctx, cudaGetLastError());
+    const cudaMemcpyKind k_out = o.host_buffers ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    HISQ_CUDA(ctx, cudaMemcpyAsync(x, w.x64, vb, k_out, st));
+    if ((rc = read_scalars(ctx, w, st))) return rc;
+    double worst = 0.0, worst_it = 0.0;
+    bool ok = true;
+    int iters = 0;
+    for (int r = 0; r < nrhs; r++) {
+        const Scalars &S = w.h_sc[r];
+        const double res = S.bb > 0 ? std::sqrt(S.rr / S.bb) : 0.0;
+        if (residuals) residuals[r] = res;
+        worst = std::max(worst, res);
+        worst_it = std::max(worst_it, res);
+        iters = std::max(iters, S.iters);
+        if (S.bad || !(res <= o.tol)) ok = false;
+    }
+    if (stats) {
+        stats->iterations = iters;
+        stats->reliable_updates = nru;
+        stats->true_residual = worst;
+        stats->iterated_residual = worst_it;
+        stats->seconds = wall() - t0;
+        stats->dslash_calls = dcalls + 2L * (nru + (o.zero_guess ? 0 : 1));
+        stats->dslash_ms = dms;
+        stats->dslash_timed = dtimed;
+        const LinkStore &L = ctx->links[ps];
+        const double dsl = (double)w.Vh * (16.0 * link_bytes(ps, L.nreal) + 2.0 * nrhs * spinor_bytes(ps));
+        stats->bytes_moved = 2.0 * iters * dsl;
+    }
+    if (!ok) return set_error(ctx, HISQ_ENOTCONVERGED, "hisq_cg: tolerance not reached");
+    return HISQ_OK;
+}
+
+}  // namespace hisq
+
+using namespace hisq;
+
+extern "C" {
+
+void hisq_solve_opts_default(hisq_solve_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-10;
+    o->maxiter = 100000;
+    o->prec_sloppy = HISQ_F64;
+    o->prec_precise = HISQ_F64;
+    o->reliable_interval = 100;
+    o->reliable_delta = 0.1;
+    o->zero_guess = 1;
+    o->check_interval = 50;
+    o->use_graph = 1;
+}
+
+int hisq_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const hisq_solve_opts *opts,
+            hisq_stats *stats, double *residuals)
+{
+    if (!ctx) return HISQ_EINVAL;
+    if (!b || !x || nrhs < 1 || nrhs > 64 || !(m >= 0.0)) return set_error(ctx, HISQ_EINVAL, "hisq_cg: bad argument");
+    hisq_solve_opts o;
+    if (opts) o = *opts;
+    else hisq_solve_opts_default(&o);
+    if (!(o.tol > 0.0) || o.maxiter < 1) return set_error(ctx, HISQ_EINVAL, "hisq_cg: bad tolerance or maxiter");
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    cudaSetDevice(ctx->device);
+    return run_cg(ctx, m, b, x, nrhs, o, stats, residuals);
+}
+
+}  // extern "C"

@@ -1,0 +1,6 @@
+// dslash_f16.cu -- Dslash kernels with F16 storage.
+#include "dslash_kernel.cuh"
+
+namespace hisq {
+HISQ_DSLASH_INSTANTIATE(HISQ_F16)
+}  // namespace hisq

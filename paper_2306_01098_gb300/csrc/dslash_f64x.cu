@@ -1,0 +1,6 @@
+// dslash_f64x.cu -- Dslash kernels with F64X storage.
+#include "dslash_kernel.cuh"
+
+namespace hisq {
+HISQ_DSLASH_INSTANTIATE(HISQ_F64X)
+}  // namespace hisq

@@ -1,0 +1,133 @@
+// reduce.cuh -- deterministic grid reductions with a "last block finishes" step, and the
+// per-right-hand-side scalars of the CG recurrences kept on the device.
+//
+// Each block writes one FP64 partial per value; the block that arrives last (atomic
+// counter after a fence) sums the partials of every value in a fixed order and applies a
+// finishing operation, so no host round trip or extra launch is needed between the
+// reduction and the scalar recurrences that consume it.
+#pragma once
+
+#include "internal.cuh"
+
+namespace hisq {
+
+// scalars of one right-hand side / shift, device resident
+struct Scalars {
+    double rr;      // |r|^2 of the current residual
+    double pAp;     // <p, A p>
+    double alpha;   // rr / pAp
+    double beta;    // rr_new / rr
+    double stop;    // sloppy stopping threshold on |r|^2
+    double rr_ref;  // |r|^2 at the last reliable update
+    double delta2;  // reliable-update trigger: rr < delta2 * rr_ref
+    double last;    // scratch: last reduced value
+    double bb;      // |b|^2
+    int iters;      // iterations performed while active
+    int active;     // 1 while iterating
+    int flag;       // 1: reliable update wanted (sloppy target or delta reached)
+    int bad;        // 1: non-finite or non-positive curvature seen
+    int pad;
+};
+
+enum FinishOp {
+    FIN_STORE = 0, // last = total
+    FIN_ALPHA = 1, // pAp = total; alpha = rr / pAp
+    FIN_RR = 2,    // beta = total / rr; rr = total; set flag when below stop / delta
+};
+
+struct Reduce {
+    double *partials = nullptr; // [nval][nblocks]
+    unsigned *counter = nullptr;
+    Scalars *sc = nullptr;      // nval scalars (indexed from sc_offset)
+    int op = FIN_STORE;
+    int nblocks = 0;            // partials per value (blocks along grid x)
+    int ntotal = 0;             // blocks in the grid (all must arrive before finishing)
+};
+
+__device__ __forceinline__ void finish_value(const Reduce &R, int v, double total)
+{
+    Scalars &S = R.sc[v];
+    switch (R.op) {
+    case FIN_ALPHA:
+        S.pAp = total;
+        if (S.active && !(total > 0.0 && isfinite(total))) {
+            S.bad = 1;
+            S.active = 0;
+        }
+        S.alpha = S.active ? S.rr / total : 0.0;
+        break;
+    case FIN_RR:
+        if (S.active) {
+            S.iters++;
+            if (!isfinite(total)) {
+                S.bad = 1;
+                S.active = 0;
+                S.beta = 0.0;
+                break;
+            }
+            S.beta = S.rr > 0.0 ? total / S.rr : 0.0;
+            S.rr = total;
+            if (total <= S.stop || total < S.delta2 * S.rr_ref) S.flag = 1;
+            if (total <= S.stop) S.active = 0;
+        } else {
+            S.beta = 0.0;
+        }
+        break;
+    default:
+        S.last = total;
+        break;
+    }
+}
+
+// block-wide sum of one double; result valid on thread 0
+__device__ __forceinline__ double block_sum(double x)
+{
+    __shared__ double wsum[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) wsum[w] = x;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = l < nw ? wsum[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;
+}
+
+// Grid reduction of `nval_all` values.  Block (bx, by) supplies the block sums of values
+// [vbase, vbase + nmine) (thread 0 holds them in `mine`) as partial number bx of each;
+// the last of the R.ntotal blocks to arrive sums the R.nblocks partials of every value
+// in a fixed order and applies R.op.  The counter is reset for the next use.
+template <int NV>
+__device__ __forceinline__ void grid_reduce(const Reduce &R, const double (&mine)[NV], int nmine, int vbase,
+                                            int nval_all, int bx)
+{
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        for (int v = 0; v < nmine; v++) R.partials[(size_t)(vbase + v) * R.nblocks + bx] = mine[v];
+        __threadfence();
+        const unsigned prev = atomicAdd(R.counter, 1u);
+        last = (prev == (unsigned)R.ntotal - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int v = 0; v < nval_all; v++) {
+        double x = 0.0;
+        for (int i = threadIdx.x; i < R.nblocks; i += blockDim.x)
+            x += __ldcg(R.partials + (size_t)v * R.nblocks + i);
+        x = block_sum(x);
+        if (threadIdx.x == 0) finish_value(R, v, x);
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *R.counter = 0u;
+    }
+}
+
+}  // namespace hisq

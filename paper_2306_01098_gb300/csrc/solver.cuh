@@ -1,0 +1,38 @@
+// solver.cuh -- device workspace of the Krylov solvers, cached on the context.
+#pragma once
+
+#include <vector>
+
+#include "reduce.cuh"
+
+namespace hisq {
+
+struct SolverWork {
+    int nrhs = 0, ps = -1, px = -1, pp = -1;
+    uint32_t Vh = 0;
+    size_t rbS = 0, rbX = 0, rb64 = 0, rbP = 0; // bytes per rhs: sloppy, accumulator, canonical F64, padded F64
+    char *r = nullptr, *p = nullptr, *Ap = nullptr, *t = nullptr, *xlo = nullptr; // sloppy vectors
+    char *b64 = nullptr, *x64 = nullptr, *rhi = nullptr, *Axhi = nullptr, *thi = nullptr; // FP64
+    char *xx = nullptr, *tx = nullptr, *Axx = nullptr; // float-pair precise operator
+    Scalars *sc = nullptr;
+    Scalars *h_sc = nullptr; // pinned host copy
+    double *partials = nullptr;
+    unsigned *counter = nullptr;
+    int nblk_vec = 0, nblk_dslash = 0;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_n = 0;
+    double graph_m = -1.0;
+    bool graph_prof = false;
+    std::vector<cudaEvent_t> prof;
+    std::vector<void *> allocs;
+
+    void release();
+    int alloc(hisq_ctx *ctx, char **ptr, size_t bytes);
+    Reduce red(int op, int nblocks_per_value, int ntotal = 0) const;
+};
+
+int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out);
+
+}  // namespace hisq

@@ -1,0 +1,226 @@
+"""ctypes binding of libhisq.so: the C ABI of include/hisq.h, argument marshalling only.
+
+Vectors and links are torch tensors (complex128, contiguous) whose device pointers are
+passed straight to the library; every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: importing works without a GPU, but every call needs
+the built library and a CUDA device, and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libhisq.so")
+
+F64, F64X, F32, F16, BF16 = 0, 1, 2, 3, 4
+PREC_NAMES = {F64: "f64", F64X: "f64x", F32: "f32", F16: "f16", BF16: "bf16"}
+NPREC = 5
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ETIMEOUT, EDEVICE, ENOTBUILT = range(8)
+
+_lib = None
+
+
+class HisqError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hisq error {code}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("links_on_device", ctypes.c_int), ("links_phased", ctypes.c_int),
+                ("prec_mask", ctypes.c_uint), ("compression", ctypes.c_int * NPREC),
+                ("device", ctypes.c_int)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("prec_sloppy", ctypes.c_int),
+                ("prec_precise", ctypes.c_int), ("reliable_interval", ctypes.c_int),
+                ("reliable_delta", ctypes.c_double), ("zero_guess", ctypes.c_int),
+                ("host_buffers", ctypes.c_int), ("check_interval", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("iterated_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("dslash_calls", ctypes.c_long),
+                ("dslash_ms", ctypes.c_double), ("dslash_timed", ctypes.c_long),
+                ("bytes_moved", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
+
+_SIGS = {
+    "hisq_opts_default": (None, [ctypes.POINTER(Opts)]),
+    "hisq_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_I), _P, _P, ctypes.POINTER(Opts)]),
+    "hisq_destroy": (None, [_P]),
+    "hisq_get_last_error": (_I, [_P]),
+    "hisq_last_error_message": (ctypes.c_char_p, [_P]),
+    "hisq_strerror": (ctypes.c_char_p, [_I]),
+    "hisq_half_volume": (_L, [_P]),
+    "hisq_field_create": (_I, [_P, _I, _I, ctypes.POINTER(_P)]),
+    "hisq_field_destroy": (None, [_P]),
+    "hisq_field_import": (_I, [_P, _P, _P]),
+    "hisq_field_export": (_I, [_P, _P, _P]),
+    "hisq_field_bytes": (ctypes.c_size_t, [_P]),
+    "hisq_dslash": (_I, [_P, _I, _P, _P, _I, _I, _P]),
+    "hisq_dslash_field": (_I, [_P, _I, _P, _P, _P]),
+    "hisq_mdagm": (_I, [_P, _D, _P, _P, _I, _I, _P]),
+    "hisq_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
+    "hisq_cg": (_I, [_P, _D, _P, _P, _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
+    "hisq_multishift_cg": (_I, [_P, _D, _I, _P, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
+}
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def lib():
+    """Load libhisq.so (built in-tree by build()); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError(f"{LIBPATH} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIBPATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Context:
+    """One lattice with its links prepared on the device (hisq_create)."""
+
+    def __init__(self, dims, fat, lng, precs=(F64, F64X, F32, F16), compression=None, phased=False, device=0):
+        L = lib()
+        o = Opts()
+        L.hisq_opts_default(ctypes.byref(o))
+        o.links_on_device = int(fat.is_cuda)
+        o.links_phased = int(phased)
+        o.prec_mask = sum(1 << p for p in precs)
+        o.device = device
+        for p, c in (compression or {}).items():
+            o.compression[p] = c
+        d = (ctypes.c_int * 4)(*dims)
+        h = ctypes.c_void_p()
+        rc = L.hisq_create(ctypes.byref(h), d, _ptr(fat), _ptr(lng), ctypes.byref(o))
+        if rc != OK:
+            raise HisqError(rc, L.hisq_strerror(rc).decode())
+        self.h = h
+        self.dims = tuple(dims)
+        self.Vh = L.hisq_half_volume(h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hisq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc):
+        if rc not in (OK, ENOTCONVERGED):
+            raise HisqError(rc, lib().hisq_last_error_message(self.h).decode())
+        return rc
+
+    # ------------------------------------------------------------------ operators
+    def dslash(self, out_parity, inp, out, prec=F64, stream=None):
+        nrhs = inp.numel() // (self.Vh * 3)
+        return self.check(lib().hisq_dslash(self.h, out_parity, _ptr(inp), _ptr(out), nrhs, prec, _stream(stream)))
+
+    def mdagm(self, m, inp, out, prec=F64, stream=None):
+        nrhs = inp.numel() // (self.Vh * 3)
+        return self.check(lib().hisq_mdagm(self.h, float(m), _ptr(inp), _ptr(out), nrhs, prec, _stream(stream)))
+
+    def field(self, prec, nrhs=1):
+        return Field(self, prec, nrhs)
+
+    def dslash_field(self, out_parity, fin, fout, stream=None):
+        return self.check(lib().hisq_dslash_field(self.h, out_parity, fin.h, fout.h, _stream(stream)))
+
+    # ------------------------------------------------------------------ solvers
+    @staticmethod
+    def solve_opts(**kw):
+        o = SolveOpts()
+        lib().hisq_solve_opts_default(ctypes.byref(o))
+        for k, v in kw.items():
+            if k == "stream":
+                v = _stream(v)
+            setattr(o, k, v)
+        return o
+
+    def cg(self, m, b, x, opts=None, residuals=None, **kw):
+        o = opts or self.solve_opts(**kw)
+        st = Stats()
+        nrhs = b.numel() // (self.Vh * 3)
+        rc = self.check(lib().hisq_cg(self.h, float(m), _ptr(b), _ptr(x), nrhs, ctypes.byref(o), ctypes.byref(st),
+                                      _ptr(residuals)))
+        return rc, st
+
+    def multishift_cg(self, m, sigma, b, xs, tol=None, opts=None, residuals=None, **kw):
+        o = opts or self.solve_opts(**kw)
+        st = Stats()
+        n = len(sigma)
+        sig = (ctypes.c_double * n)(*sigma)
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        tp = (ctypes.c_double * n)(*tol) if tol is not None else None
+        rc = self.check(lib().hisq_multishift_cg(self.h, float(m), n, sig, _ptr(b), xp, tp, ctypes.byref(o),
+                                                 ctypes.byref(st), _ptr(residuals)))
+        return rc, st
+
+
+class Field:
+    """Internal-layout vectors of one precision (hisq_field_*)."""
+
+    def __init__(self, ctx: Context, prec: int, nrhs: int = 1):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx.check(lib().hisq_field_create(ctx.h, prec, nrhs, ctypes.byref(h)))
+        self.h, self.prec, self.nrhs = h, prec, nrhs
+
+    def load(self, src, stream=None):
+        self.ctx.check(lib().hisq_field_import(self.h, _ptr(src), _stream(stream)))
+
+    def store(self, dst, stream=None):
+        self.ctx.check(lib().hisq_field_export(self.h, _ptr(dst), _stream(stream)))
+
+    def nbytes(self):
+        return lib().hisq_field_bytes(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hisq_field_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

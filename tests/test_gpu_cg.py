@@ -1,0 +1,144 @@
+"""GPU CG (through the C ABI) against the FP64 oracle.
+
+Pass criterion for every solve: the oracle recomputes |b - A x| / |b| from the GPU's x in
+FP64 and it must be <= tol (1e-10).  The relative difference from the oracle's own CG
+solution is bounded by kappa(A) * tol (both solutions sit within tol of the exact one in
+the residual norm); it is asserted against that bound and printed.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from hisq_inputs import fields
+
+hisq = pytest.importorskip("paper_2306_01098_gb300.hisq")
+
+pytestmark = pytest.mark.gpu
+
+_cache = {}
+
+
+def setup(dims, eps, seed, precs=(hisq.F64, hisq.F64X, hisq.F32, hisq.F16, hisq.BF16), comp=None):
+    key = (dims, eps, seed, precs, tuple(sorted((comp or {}).items())))
+    if key not in _cache:
+        _cache.clear()
+        fat, lng = fields.recipe_links(dims, eps, seed)
+        ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=precs, compression=comp)
+        _cache[key] = (ctx, fat.numpy(), lng.numpy())
+    return _cache[key]
+
+
+def true_res(dims, fat, lng, m, b, x):
+    r = b - oracle.mdagm(dims, fat, lng, m, x)
+    return float(np.linalg.norm(r) / np.linalg.norm(b))
+
+
+def test_plain_fp64_cg_small_workload():
+    # 8^4, eps = 0.3, m = 0.1, 1 RHS, tol 1e-10
+    dims, m = (8, 8, 8, 8), 0.1
+    ctx, fat, lng = setup(dims, 0.3, 1000)
+    b = fields.gaussian_source(dims, 2000)[0]
+    x = torch.zeros_like(b).cuda()
+    rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=hisq.F64, prec_precise=hisq.F64)
+    assert rc == hisq.OK
+    xg = x.cpu().numpy()
+    assert true_res(dims, fat, lng, m, b.numpy(), xg) <= 1e-10
+    xo, it_o, _, _ = oracle.cg(dims, fat, lng, m, b.numpy(), tol=1e-10)
+    assert abs(st.iterations - it_o) <= 2
+    rel = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    kappa = (4 * (m * m + 4 * (1 + 1 / 24) ** 2)) / (4 * m * m)
+    print(f"plain FP64: iterations {st.iterations} (oracle {it_o}), rel. diff vs oracle {rel:.2e}")
+    assert rel <= kappa * 1e-10
+
+
+@pytest.mark.parametrize("sloppy,precise", [(hisq.F32, hisq.F64), (hisq.F16, hisq.F64), (hisq.BF16, hisq.F64),
+                                            (hisq.F64X, hisq.F64X), (hisq.F32, hisq.F64X), (hisq.F16, hisq.F64X)])
+def test_mixed_precision_cg(sloppy, precise):
+    dims, m = (8, 8, 8, 12), 0.02
+    ctx, fat, lng = setup(dims, 0.5, 1001)
+    b = fields.gaussian_source(dims, 2100)[0]
+    x = torch.zeros_like(b).cuda()
+    rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=sloppy, prec_precise=precise, reliable_interval=100)
+    assert rc == hisq.OK, st.as_dict()
+    res = true_res(dims, fat, lng, m, b.numpy(), x.cpu().numpy())
+    print(f"sloppy {hisq.PREC_NAMES[sloppy]} precise {hisq.PREC_NAMES[precise]}: iterations {st.iterations}, "
+          f"reliable updates {st.reliable_updates}, true residual {res:.2e}")
+    assert res <= 1e-10
+    assert st.true_residual <= 1e-10
+
+
+@pytest.mark.parametrize("nrhs,sloppy", [(2, hisq.F64), (4, hisq.F32), (3, hisq.F16), (8, hisq.F32)])
+def test_multi_rhs_cg(nrhs, sloppy):
+    dims, m = (6, 6, 6, 8), 0.05
+    ctx, fat, lng = setup(dims, 0.5, 1010)
+    b = fields.gaussian_source(dims, 2150, nrhs)
+    x = torch.zeros_like(b).cuda()
+    res_out = torch.zeros(nrhs, dtype=torch.float64)
+    rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=sloppy, prec_precise=hisq.F64, residuals=res_out)
+    assert rc == hisq.OK
+    xg = x.cpu().numpy()
+    for r in range(nrhs):
+        assert true_res(dims, fat, lng, m, b[r].numpy(), xg[r]) <= 1e-10
+        assert res_out[r] <= 1e-10
+
+
+def test_initial_guess_and_host_buffers():
+    dims, m = (8, 4, 6, 8), 0.05
+    ctx, fat, lng = setup(dims, 0.5, 1011)
+    b = fields.gaussian_source(dims, 2160)[0]
+    x0 = (0.1 * fields.gaussian_source(dims, 2161)[0]).contiguous()
+    x = x0.clone().pin_memory()
+    bp = b.clone().pin_memory()
+    rc, st = ctx.cg(m, bp, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, zero_guess=0, host_buffers=1)
+    assert rc == hisq.OK
+    assert true_res(dims, fat, lng, m, b.numpy(), x.numpy()) <= 1e-10
+
+
+def test_graph_and_direct_launch_agree():
+    dims, m = (8, 8, 8, 8), 0.05
+    ctx, fat, lng = setup(dims, 0.5, 1012)
+    b = fields.gaussian_source(dims, 2170)[0].cuda()
+    xs = []
+    for g in (0, 1):
+        x = torch.zeros_like(b)
+        rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, use_graph=g, check_interval=20)
+        assert rc == hisq.OK
+        xs.append((x.cpu(), st.iterations))
+    assert xs[0][1] == xs[1][1]
+    assert torch.equal(xs[0][0], xs[1][0])           # same kernels, same order: bitwise
+
+
+def test_profiled_solve_counts_dslash_launches():
+    dims, m = (8, 8, 8, 8), 0.05
+    ctx, fat, lng = setup(dims, 0.5, 1012)
+    b = fields.gaussian_source(dims, 2171)[0].cuda()
+    x = torch.zeros_like(b)
+    rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, profile=1, check_interval=10)
+    assert rc == hisq.OK
+    assert st.dslash_timed == 2 * st.iterations and st.dslash_ms > 0
+
+
+def test_not_converged_and_nan_source():
+    dims, m = (8, 8, 8, 8), 0.01
+    ctx, fat, lng = setup(dims, 0.5, 1013)
+    b = fields.gaussian_source(dims, 2180)[0].cuda()
+    x = torch.zeros_like(b)
+    rc, st = ctx.cg(m, b, x, tol=1e-10, maxiter=7, prec_sloppy=hisq.F32, prec_precise=hisq.F64)
+    assert rc == hisq.ENOTCONVERGED and st.iterations == 7
+    bn = b.clone()
+    bn[5, 1] = float("nan")
+    rc, st = ctx.cg(m, bn, torch.zeros_like(b), tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64)
+    assert rc == hisq.ENOTCONVERGED
+    # the context stays usable
+    rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64)
+    assert rc == hisq.OK
+
+
+def test_zero_source_returns_zero():
+    dims, m = (4, 4, 4, 4), 0.1
+    ctx, fat, lng = setup(dims, 0.5, 1014)
+    b = torch.zeros(ctx.Vh, 3, dtype=torch.complex128, device="cuda")
+    x = torch.ones_like(b)
+    rc, st = ctx.cg(m, b, x, tol=1e-10)
+    assert x.abs().max().item() == 0.0 and st.iterations == 0
