@@ -37,6 +37,13 @@ template <int P> struct Blas {
 #pragma unroll
         for (int i = 0; i < 6; i++) y.v[i] = br * y.v[i] + x.v[i];
     }
+    // y = a x + b y
+    __device__ static void axpby(Vec &y, double a, const Vec &x, double b)
+    {
+        const typename T::Real ar = (typename T::Real)a, br = (typename T::Real)b;
+#pragma unroll
+        for (int i = 0; i < 6; i++) y.v[i] = ar * x.v[i] + br * y.v[i];
+    }
     __device__ static double norm2(const Vec &x)
     {
         typename T::Real s = 0;
@@ -77,6 +84,20 @@ template <> struct Blas<HISQ_F64X> {
 #pragma unroll
         for (int i = 0; i < 6; i++) {
             DAcc c = {x.h[i], x.l[i]};
+            dd_mac(c, bh, bl, y.h[i], y.l[i]);
+            const DD d = dd_norm(c);
+            y.h[i] = d.h;
+            y.l[i] = d.l;
+        }
+    }
+    __device__ static void axpby(Vec &y, double a, const Vec &x, double b)
+    {
+        const float ah = (float)a, al = (float)(a - (double)ah);
+        const float bh = (float)b, bl = (float)(b - (double)bh);
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            DAcc c = {0.f, 0.f};
+            dd_mac(c, ah, al, x.h[i], x.l[i]);
             dd_mac(c, bh, bl, y.h[i], y.l[i]);
             const DD d = dd_norm(c);
             y.h[i] = d.h;
@@ -155,11 +176,10 @@ __global__ void __launch_bounds__(kVecBlock) k_update_xp(VecRef x, VecRef p, Vec
         typename BS::Vec pv;
         vload<PS>(pp, s, pv);
         if (do_x) {
-            typename BX::Vec xv, pc;
+            static_assert(std::is_same<typename BS::Vec, typename BX::Vec>::value, "shared vector type");
+            typename BX::Vec xv;
             vload<PX>(xp, s, xv);
-#pragma unroll
-            for (int i = 0; i < 6; i++) BX::set(pc, i, BS::get(pv, i));
-            BX::axpy(xv, alpha, pc);
+            BX::axpy(xv, alpha, pv);
             BX::store(xp, s, xv);
         }
         if (do_p) {
@@ -229,7 +249,7 @@ __global__ void __launch_bounds__(kVecBlock) k_residual(VecRef b, VecRef Ax, Vec
 }
 
 // |x|^2 (F64) reduced with FIN_STORE
-__global__ void __launch_bounds__(kVecBlock) k_norm_f64(VecRef x, uint32_t Vh, Reduce red)
+static __global__ void __launch_bounds__(kVecBlock) k_norm_f64(VecRef x, uint32_t Vh, Reduce red)
 {
     const int rhs = blockIdx.y;
     double acc = 0.0;

@@ -317,6 +317,7 @@ void hisq_destroy(hisq_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     release_work(ctx);
+    release_ms_work(ctx);
     for (auto &L : ctx->links)
         if (L.base) cudaFree(L.base);
     if (ctx->ws) cudaFree(ctx->ws);

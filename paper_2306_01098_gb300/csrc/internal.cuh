@@ -178,6 +178,7 @@ struct DevStatus {
 };
 
 struct SolverWork;
+struct MsWork;
 
 }  // namespace hisq
 
@@ -196,6 +197,7 @@ struct hisq_ctx {
     size_t ws_bytes = 0;
     hisq::DevStatus *status = nullptr;
     hisq::SolverWork *solver = nullptr; // cached solver workspace
+    hisq::MsWork *msolver = nullptr;    // cached multi-shift workspace
 };
 
 struct hisq_field {
@@ -212,6 +214,7 @@ int set_error(hisq_ctx *ctx, int code, const std::string &msg);
 int cuda_error(hisq_ctx *ctx, cudaError_t e, const char *what);
 int ensure_workspace(hisq_ctx *ctx, size_t bytes);
 void release_work(hisq_ctx *ctx);
+void release_ms_work(hisq_ctx *ctx);
 
 #define HISQ_CUDA(ctx, call)                                      \
     do {                                                          \
