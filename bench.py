@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark: HISQ even-odd CG time to a 1e-10 true residual on one GB300, mixed precision vs
+plain FP64, with the sloppy Dslash's HBM roofline fraction.
+
+Workload (default): 32^3 x 8 lattice, seeded SU(3) links U = exp(i 0.5 H), fat = U,
+long = -1/24 U U U, m = 0.01, one Gaussian source on even sites, tol 1e-10 on the
+recomputed FP64 residual.  One step = one complete solve with inputs resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 runs N independent replicas (one per GPU, launched
+by torch.distributed.run); value is the max-over-ranks time per solve.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GB/s vs HBM peak; CG time to 1e-10 true residual vs plain FP64 CG"
+WORKLOAD = "mixed-precision even-odd CG, 32^3x8, eps=0.5, m=0.01, 1 RHS, tol 1e-10"
+DIMS, EPS, LINK_SEED, SRC_SEED, MASS, TOL = (32, 32, 32, 8), 0.5, 1001, 2100, 0.01, 1e-10
+HBM_FALLBACK = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu, self.rows, self.proc = gpu, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------------------- oracle
+def oracle_sample(seconds_budget: float, fp64_iters: int):
+    """Time the FP64 oracle's CG iterations on the host cores; scale to a full solve."""
+    import numpy as np
+
+    import oracle
+    from hisq_inputs import fields
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    fat, lng = fields.recipe_links(DIMS, EPS, LINK_SEED)
+    b = fields.gaussian_source(DIMS, SRC_SEED)[0].numpy()
+    fat, lng = fat.numpy(), lng.numpy()
+    oracle.cg_fixed(DIMS, fat, lng, MASS, b, 1)            # warm
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.cg_fixed(DIMS, fat, lng, MASS, b, 10)
+        done += 10
+        el = time.perf_counter() - t0
+        if el >= seconds_budget or done >= 2000:
+            break
+    per_iter_ms = 1e3 * el / done
+    return {"value": per_iter_ms * fp64_iters, "unit": "ms", "cores": threads, "kind": "oracle",
+            "sample": f"{done} FP64 oracle CG iterations on 32^3x8 ({el:.1f} s, {threads} threads), "
+                      f"scaled to the {fp64_iters} iterations of the GPU's plain FP64 solve",
+            "per_iteration_ms": per_iter_ms}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the FP64 oracle as it stands, on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    # iteration count of the FP64 solve: from one full oracle solve (untimed)
+    import oracle
+    from hisq_inputs import fields
+    oracle.set_threads(os.cpu_count() or 1)
+    fat, lng = fields.recipe_links(DIMS, EPS, LINK_SEED)
+    b = fields.gaussian_source(DIMS, SRC_SEED)[0].numpy()
+    _, fp64_iters, _, true_res = oracle.cg(DIMS, fat.numpy(), lng.numpy(), MASS, b, tol=TOL)
+    samples = []
+    for _ in range(args.warmup):
+        oracle_sample(2.0, fp64_iters)
+    for _ in range(args.steps):
+        samples.append(oracle_sample(max(3.0, 60.0 / max(1, args.steps)), fp64_iters))
+    v = statistics.mean(s["value"] for s in samples)
+    cb = dict(samples[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (FP64 oracle on host cores, extrapolated)"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "iterations": fp64_iters, "true_residual": true_res}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------- GPU arm
+def traffic_for(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel_key]
+        h = hashlib.sha256()
+        for fn in e["sources"]:
+            with open(os.path.join(ROOT, fn), "rb") as g:
+                h.update(g.read())
+        return e["dram_bytes_per_launch"] if h.hexdigest() == e["sha256"] else None
+    except Exception:
+        return None
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(world)
+    from hisq_inputs import fields
+    from paper_2306_01098_gb300 import hisq
+
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    fat, lng = fields.recipe_links(DIMS, EPS, LINK_SEED, device=dev)
+    sloppy = {"f32": hisq.F32, "f16": hisq.F16, "bf16": hisq.BF16, "f64x": hisq.F64X}[args.sloppy]
+    ctx = hisq.Context(DIMS, fat, lng, precs=(hisq.F64, hisq.F64X, hisq.F32, hisq.F16, hisq.BF16), device=local)
+    del fat, lng
+    b = fields.gaussian_source(DIMS, SRC_SEED, device=dev)[0]
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def solve(prec, precise=hisq.F64, profile=0, xb=x, bb=b, host=0):
+        rc, st = ctx.cg(MASS, bb, xb, tol=TOL, prec_sloppy=prec, prec_precise=precise, reliable_interval=100,
+                        reliable_delta=0.1, profile=profile, host_buffers=host, stream=stream)
+        if rc != hisq.OK:
+            raise RuntimeError(f"solve did not converge: {st.as_dict()}")
+        return st
+
+    # plain FP64 CG on the same GPU (the comparator), outside the timed region
+    solve(hisq.F64)
+    x64 = x.clone()
+    fp64_ms = []
+    for _ in range(args.fp64_reps):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st64 = solve(hisq.F64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms.append(e0.elapsed_time(e1))
+    fp64_ms = min(fp64_ms) if fp64_ms else None
+
+    for _ in range(args.warmup):
+        flush.add_(1.0)
+        solve(sloppy)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    stats = []
+    torch.cuda.nvtx.range_push("timed")
+    with Clocks(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        step_ms = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.add_(1.0)                       # L2 flushed between timed solves
+            s0.record(stream)
+            stats.append(solve(sloppy, profile=1))
+            s1.record(stream)
+            s1.synchronize()
+            step_ms.append(s0.elapsed_time(s1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    barrier(world)
+    total_ms = e0.elapsed_time(e1)
+    ms_per_solve = max_over_ranks(sum(step_ms) / len(step_ms), world)
+
+    # end to end through the C ABI with host buffers: H2D of b, D2H of x inside the timed region
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    solve(sloppy, xb=xh, bb=bh, host=1)
+    torch.cuda.synchronize()
+    e2e = []
+    for _ in range(args.e2e_steps if args.e2e_steps is not None else args.steps):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solve(sloppy, xb=xh, bb=bh, host=1)
+        torch.cuda.synchronize()
+        e2e.append(1e3 * (time.perf_counter() - t0))
+    e2e_ms = max_over_ranks(statistics.mean(e2e), world) if e2e else None
+
+    # accuracy of the mixed-precision result against the FP64 solve
+    err_vs_fp64 = float(((x - x64).norm() / x64.norm()).item())
+    st = stats[-1]
+    Vh = ctx.Vh
+    lb = {hisq.F32: 72, hisq.F16: 36, hisq.BF16: 36, hisq.F64X: 144}[sloppy]
+    sb = {hisq.F32: 24, hisq.F16: 16, hisq.BF16: 16, hisq.F64X: 48}[sloppy]
+    bytes_per_launch = Vh * (16 * lb + 2 * sb)
+    d_ms = sum(s.dslash_ms for s in stats) / max(1, sum(s.dslash_timed for s in stats))
+    hbm, src = peaks()
+    achieved = bytes_per_launch / (d_ms * 1e-3) / 1e9
+    kname = f"dslash_{args.sloppy}_18_32x32x32x8"
+    clocks = clk.summary()
+    if rank != 0:
+        return
+    table = None
+    if not args.no_dslash_table:
+        from paper_2306_01098_gb300 import dslash_bench
+        table = dslash_bench.measure((64, 64, 64, 16), ("f64", "f64x", "f32", "f16"), (1,), 18, hbm_gbs=hbm)
+    cb = oracle_sample(args.cpu_seconds, st64.iterations) if not args.no_cpu_baseline else None
+    line = {
+        "metric": METRIC, "value": ms_per_solve, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_solve, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": f"{args.sloppy}+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "32x32x32x8", "sloppy": args.sloppy, "precise": "f64",
+                   "reliable_interval": 100, "l2": "flushed between timed solves (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "iterations": st.iterations, "reliable_updates": st.reliable_updates, "true_residual": st.true_residual,
+        "error_vs_fp64": err_vs_fp64, "fp64_cg_ms": fp64_ms, "fp64_iterations": st64.iterations,
+        "speedup_vs_fp64_cg": fp64_ms / ms_per_solve if fp64_ms else None, "timed_total_ms": total_ms,
+        "dslash_64x64x64x16": table,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic_for(kname), "kernel": kname, "peak_source": src,
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": d_ms * 1e3,
+                     "launches_timed": sum(s.dslash_timed for s in stats)},
+        "cpu_baseline": cb,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(b.numel() * 16),
+                "d2h_bytes_per_step": int(b.numel() * 16)},
+        "gpu_launches": int(sum(s.kernels for s in stats)) + args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sloppy", default="f32", choices=["f32", "f16", "bf16", "f64x"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dslash-table", action="store_true")
+    ap.add_argument("--fp64-reps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

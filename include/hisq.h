@@ -17,8 +17,9 @@
  *             of the spinors (Sec. 3), unless hisq_opts.links_phased = 1.
  *   Vectors   one parity, complex128 [nrhs][Vh][3] in canonical half-index order.
  *   Streams   `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
- *             Dslash / normal-operator calls are stream-ordered and asynchronous; solver
- *             calls synchronise their stream before returning.
+ *             Dslash / normal-operator calls are stream-ordered and asynchronous.  Solver
+ *             calls run on an internal stream that first waits for `stream`, synchronise
+ *             before returning, and make `stream` wait for their completion.
  *   Errors    every int-returning call returns HISQ_OK (0) or one of the codes below and
  *             records it with a message on the context (hisq_get_last_error,
  *             hisq_last_error_message).  Nothing throws across the ABI.
@@ -154,7 +155,8 @@ typedef struct {
     long dslash_calls;       /* Dslash applications (all precisions)                          */
     double dslash_ms;        /* summed event time of the timed sloppy Dslash launches         */
     long dslash_timed;       /* number of timed launches (profile = 1)                        */
-    double bytes_moved;      /* algorithmic bytes of all kernels (links + vectors)            */
+    double bytes_moved;      /* algorithmic bytes of the sloppy Dslash applications           */
+    long kernels;            /* kernel launches issued by the call (graph nodes included)     */
 } hisq_stats;
 
 void hisq_solve_opts_default(hisq_solve_opts *o);

@@ -97,6 +97,26 @@ __device__ __forceinline__ DD dd_norm(DAcc a)
     return {hi, lo};
 }
 
+// fold the error term back into the running sum (keeps |e| <= ulp(h) / 2)
+__device__ __forceinline__ void dd_renorm(DAcc &a)
+{
+    const DD d = dd_norm(a);
+    a.h = d.h;
+    a.e = d.l;
+}
+
+// a += b for two compensated sums (TwoSum of the leading parts, then renormalise)
+__device__ __forceinline__ void dd_add(DAcc &a, const DAcc &b)
+{
+    const float s = __fadd_rn(a.h, b.h);
+    const float z = __fsub_rn(s, a.h);
+    float t = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, z)), __fsub_rn(b.h, z));
+    t = __fadd_rn(t, __fadd_rn(a.e, b.e));
+    const float hi = __fadd_rn(s, t);
+    a.h = hi;
+    a.e = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
 // ---------------------------------------------------------------- precision traits
 template <int P> struct Prec;
 
@@ -186,6 +206,8 @@ template <> struct Prec<HISQ_F64> {
 #pragma unroll
         for (int i = 0; i < 6; i++) o.v[i] = fma(m4, p.v[i], -o.v[i]);
     }
+    static constexpr bool kSplitDirections = false;
+    __device__ static void add_acc(Acc &, const Acc &) {}
     // Re <p, o>
     __device__ static double dot(const Vec &p, const Acc &o)
     {
@@ -250,6 +272,8 @@ struct FloatArith {
 #pragma unroll
         for (int i = 0; i < 6; i++) out.v[i] = fmaf(a, x.v[i], out.v[i]);
     }
+    static constexpr bool kSplitDirections = false;
+    __device__ static void add_acc(Acc &, const Acc &) {}
     __device__ static void mdagm_epilogue(Acc &o, double m4, const Vec &p)
     {
         const float m = (float)m4;
@@ -411,6 +435,17 @@ template <> struct Prec<HISQ_F64X> {
                 dd_mac(a.v[2 * i + 1], urh, url, v.h[2 * j + 1], v.l[2 * j + 1]);
                 dd_mac(a.v[2 * i + 1], uih, uil, v.h[2 * j], v.l[2 * j]);
             }
+        // one renormalisation per hop (every six products of a component)
+#pragma unroll
+        for (int c = 0; c < 6; c++) dd_renorm(a.v[c]);
+    }
+    // directions are summed separately (24 products each) and combined pairwise: the
+    // rounding error of a compensated sum grows with the number of terms it absorbs
+    static constexpr bool kSplitDirections = true;
+    __device__ static void add_acc(Acc &a, const Acc &b)
+    {
+#pragma unroll
+        for (int c = 0; c < 6; c++) dd_add(a.v[c], b.v[c]);
     }
     __device__ static void rebuild(Link &, bool) {}
     __device__ static void axpy_acc(Acc &, double, const Acc &) {}

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kVecBlock) k_update_r(VecRef r, VecRef Ap, uin
 {
     using B = Blas<PS>;
     const int rhs = blockIdx.y;
-    const double alpha = red.sc[rhs].alpha;
+    const double alpha = alpha_fresh_for_r(red.sc[rhs]) ? red.sc[rhs].alpha : 0.0;
     double acc = 0.0;
     if (alpha != 0.0) {
         char *rp = r.rhs(rhs);
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kVecBlock) k_update_xp(VecRef x, VecRef p, Vec
     using BS = Blas<PS>;
     using BX = Blas<PX>;
     const int rhs = blockIdx.y;
-    const double alpha = sc[rhs].alpha, beta = sc[rhs].beta;
+    const double alpha = alpha_fresh_for_x(sc[rhs]) ? sc[rhs].alpha : 0.0, beta = sc[rhs].beta;
     const bool do_x = mode != 2 && alpha != 0.0;
     const bool do_p = mode != 1 && sc[rhs].active;
     if (!do_x && !do_p) return;

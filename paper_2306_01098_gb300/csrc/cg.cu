@@ -42,6 +42,8 @@ __global__ void k_scalars(Scalars *sc, int n, int mode, double tol2, double delt
         S.stop = tol2 * S.last;
         S.delta2 = delta2;
         S.iters = 0;
+        S.it_all = 0;
+        S.astamp = -2;
         S.bad = 0;
         break;
     case SC_INIT_R:
@@ -344,6 +346,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
     }
     int total = 0, since_ru = 0, nru = 0, prev_iters = 0;
+    long kernels = 6 + (o.zero_guess ? 0 : 3); // setup: norms, scalars, conversions (+ residual)
     long dcalls = 0;
     double dms = 0.0;
     long dtimed = 0;
@@ -381,6 +384,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         }
         total += n;
         since_ru += n;
+        kernels += 4L * n;
         if ((rc = read_scalars(ctx, w, st))) return rc;
         int it = 0;
         bool any_active = false, any_flag = false;
@@ -408,6 +412,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             if ((rc = precise_residual(ctx, w, m, st))) return rc;
             k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_RU, tol2, delta2);
             dispatch(ps, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
+            kernels += 5 + (w.pp == HISQ_F64X ? 1 : 0);
             nru++;
             since_ru = 0;
             if ((rc = read_scalars(ctx, w, st))) return rc;
@@ -416,6 +421,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             if (!any || last) break;
         }
         dispatch(ps, [&](auto T) { decltype(T)::update_xp(w, 2, st); });
+        kernels++;
     }
     // every exit from the loop follows a reliable update (or no iteration at all), so
     // x_hi holds the whole solution and Scalars.rr its recomputed residual
@@ -423,6 +429,9 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
     const cudaMemcpyKind k_out = o.host_buffers ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     HISQ_CUDA(ctx, cudaMemcpyAsync(x, w.x64, vb, k_out, st));
     if ((rc = read_scalars(ctx, w, st))) return rc;
+    // later work on the caller's stream is ordered after the solve
+    HISQ_CUDA(ctx, cudaEventRecord(w.ev, st));
+    HISQ_CUDA(ctx, cudaStreamWaitEvent(ust, w.ev, 0));
     double worst = 0.0, worst_it = 0.0;
     bool ok = true;
     int iters = 0;
@@ -447,6 +456,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         const LinkStore &L = ctx->links[ps];
         const double dsl = (double)w.Vh * (16.0 * link_bytes(ps, L.nreal) + 2.0 * nrhs * spinor_bytes(ps));
         stats->bytes_moved = 2.0 * iters * dsl;
+        stats->kernels = kernels;
     }
     if (!ok) return set_error(ctx, HISQ_ENOTCONVERGED, "hisq_cg: tolerance not reached");
     return HISQ_OK;

@@ -46,8 +46,14 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
 #pragma unroll
             for (int r = 0; r < NR; r++) T::zero(acc[t][r]);
 
+        constexpr bool SPLIT = T::kSplitDirections;
 #pragma unroll
         for (int mu = 0; mu < 4; mu++) {
+            typename T::Acc dacc[SPLIT ? NR : 1];
+            if constexpr (SPLIT) {
+#pragma unroll
+                for (int r = 0; r < NR; r++) T::zero(dacc[r]);
+            }
 #pragma unroll
             for (int h = 0; h < 4; h++) {
                 const int k = h == 0 ? 1 : h == 1 ? -1 : h == 2 ? 3 : -3;
@@ -66,8 +72,16 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
                 for (int r = 0; r < NR; r++) {
                     typename T::Vec v;
                     T::load(a.in + (size_t)(rhs0 + r) * a.rhs_bytes, sn, v);
-                    if (back) T::template hop<true, true>(acc[TWO ? type : 0][r], U, v);
-                    else T::template hop<false, false>(acc[TWO ? type : 0][r], U, v);
+                    typename T::Acc &dst = SPLIT ? dacc[SPLIT ? r : 0] : acc[TWO ? type : 0][r];
+                    if (back) T::template hop<true, true>(dst, U, v);
+                    else T::template hop<false, false>(dst, U, v);
+                }
+            }
+            if constexpr (SPLIT) {
+#pragma unroll
+                for (int r = 0; r < NR; r++) {
+                    if (mu == 0) acc[0][r] = dacc[r];
+                    else T::add_acc(acc[0][r], dacc[r]);
                 }
             }
         }

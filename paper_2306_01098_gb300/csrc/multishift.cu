@@ -97,7 +97,8 @@ __global__ void k_shift_init(ShiftState *ss, const Scalars *sc, int n)
 __global__ void k_shift_scalars(ShiftState *ss, const Scalars *sc, int n)
 {
     const int s = threadIdx.x;
-    const double alpha = sc->alpha, beta = sc->beta;
+    // alpha and beta of this iteration, or nothing when the base launch was skipped
+    const double alpha = (sc->astamp == sc->it_all - 1) ? sc->alpha : 0.0, beta = sc->beta;
     __syncthreads();
     if (s < n) {
         if (alpha == 0.0 || !ss->active[s]) {
@@ -296,6 +297,8 @@ __global__ void k_ms_init_scalars(Scalars *sc, double tol2)
     S.alpha = S.beta = 0.0;
     S.flag = 0;
     S.iters = 0;
+    S.it_all = 0;
+    S.astamp = -2;
     S.bad = !isfinite(S.last);
     S.active = isfinite(S.last) && S.last > S.stop;
 }

@@ -23,11 +23,20 @@ struct Scalars {
     double last;    // scratch: last reduced value
     double bb;      // |b|^2
     int iters;      // iterations performed while active
+    int it_all;     // iterations launched (advanced by every |r|^2 reduction)
+    int astamp;     // it_all of the iteration whose <p,Ap> produced alpha
     int active;     // 1 while iterating
     int flag;       // 1: reliable update wanted (sloppy target or delta reached)
     int bad;        // 1: non-finite or non-positive curvature seen
     int pad;
 };
+
+// alpha is consumed only in the iteration that produced it: the residual update requires
+// astamp == it_all (before the |r|^2 reduction advances it_all), the solution update
+// astamp == it_all - 1.  When every right-hand side has converged the operator launches
+// return at once, alpha is not refreshed, and the stamps keep the updates from reusing it.
+__device__ __forceinline__ bool alpha_fresh_for_r(const Scalars &S) { return S.active && S.astamp == S.it_all; }
+__device__ __forceinline__ bool alpha_fresh_for_x(const Scalars &S) { return S.astamp == S.it_all - 1; }
 
 enum FinishOp {
     FIN_STORE = 0, // last = total
@@ -50,6 +59,7 @@ __device__ __forceinline__ void finish_value(const Reduce &R, int v, double tota
     switch (R.op) {
     case FIN_ALPHA:
         S.pAp = total;
+        S.astamp = S.it_all;
         if (S.active && !(total > 0.0 && isfinite(total))) {
             S.bad = 1;
             S.active = 0;
@@ -57,6 +67,7 @@ __device__ __forceinline__ void finish_value(const Reduce &R, int v, double tota
         S.alpha = S.active ? S.rr / total : 0.0;
         break;
     case FIN_RR:
+        S.it_all++;
         if (S.active) {
             S.iters++;
             if (!isfinite(total)) {

@@ -1,0 +1,85 @@
+"""Dslash throughput on internal-layout fields: GB/s against the HBM roofline, TFLOP/s.
+
+  python -m paper_2306_01098_gb300.dslash_bench --dims 64,64,64,16 --prec f64x,f32 --nrhs 1,4 [--comp 12]
+
+Algorithmic bytes per application (Sec. 5.1 accounting with perfect neighbour reuse):
+  Vh * (16 * link_bytes + nrhs * 2 * spinor_bytes)
+i.e. every link read once, every input and output spinor once; flops 1146 per site and
+right-hand side.  Inputs are larger than L2 at 64^3 x 16; L2 is also flushed between reps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NAMES = {"f64": 0, "f64x": 1, "f32": 2, "f16": 3, "bf16": 4}
+LINK_REAL_BYTES = {0: 8, 1: 8, 2: 4, 3: 2, 4: 2}
+SPINOR_BYTES = {0: 48, 1: 48, 2: 24, 3: 16, 4: 16}
+
+
+def alg_bytes(Vh, prec, nreal, nrhs):
+    return Vh * (16 * nreal * LINK_REAL_BYTES[prec] + nrhs * 2 * SPINOR_BYTES[prec])
+
+
+def measure(dims=(64, 64, 64, 16), precs=("f64", "f64x", "f32", "f16"), nrhs_list=(1,), comp=18, reps=10,
+            hbm_gbs=6763.3, seed=1002):
+    import torch
+
+    from hisq_inputs import fields
+    from paper_2306_01098_gb300 import hisq
+    ps = [NAMES[p] for p in precs if not (p == "f64x" and comp == 12)]
+    fat, lng = fields.recipe_links(dims, 0.3, seed, device="cuda")
+    ctx = hisq.Context(dims, fat, lng, precs=tuple(ps), compression={p: comp for p in ps})
+    del fat, lng
+    torch.cuda.empty_cache()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = []
+    for p in ps:
+        for nrhs in nrhs_list:
+            fi, fo = ctx.field(p, nrhs), ctx.field(p, nrhs)
+            fi.load(fields.gaussian_source(dims, 7, nrhs, device="cuda"))
+            for _ in range(3):
+                ctx.dslash_field(0, fi, fo)
+            torch.cuda.synchronize()
+            ts = []
+            for it in range(reps):
+                flush.add_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.dslash_field(it & 1, fi, fo)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = sorted(ts)[len(ts) // 2]
+            b = alg_bytes(ctx.Vh, p, comp, nrhs)
+            out.append({"prec": hisq.PREC_NAMES[p], "nreal": comp, "nrhs": nrhs, "us": ms * 1e3,
+                        "gbs": b / ms / 1e6, "frac_hbm": b / ms / 1e6 / hbm_gbs,
+                        "tflops": 1146 * ctx.Vh * nrhs / ms / 1e9, "bytes": b})
+            fi.close()
+            fo.close()
+    ctx.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", default="64,64,64,16")
+    ap.add_argument("--prec", default="f64,f64x,f32,f16")
+    ap.add_argument("--nrhs", default="1")
+    ap.add_argument("--comp", type=int, default=18)
+    ap.add_argument("--reps", type=int, default=10)
+    a = ap.parse_args()
+    rows = measure(tuple(int(v) for v in a.dims.split(",")), tuple(a.prec.split(",")),
+                   tuple(int(v) for v in a.nrhs.split(",")), a.comp, a.reps)
+    for r in rows:
+        print(json.dumps(r))
+
+
+if __name__ == "__main__":
+    main()

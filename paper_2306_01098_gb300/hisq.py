@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
                 ("true_residual", ctypes.c_double), ("iterated_residual", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("dslash_calls", ctypes.c_long),
                 ("dslash_ms", ctypes.c_double), ("dslash_timed", ctypes.c_long),
-                ("bytes_moved", ctypes.c_double)]
+                ("bytes_moved", ctypes.c_double), ("kernels", ctypes.c_long)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
