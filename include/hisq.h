@@ -142,7 +142,8 @@ typedef struct {
     int host_buffers;      /* 1: b and x are host pointers (copied inside the call)          */
     int check_interval;    /* iterations between host-side convergence checks (default 50)   */
     int use_graph;         /* 1: replay iteration blocks as a captured CUDA graph            */
-    int profile;           /* 1: time every sloppy Dslash launch with CUDA events            */
+    int profile;           /* 1: time the sloppy Dslash pair of the first iteration of every
+                              block of check_interval iterations with CUDA events            */
     void *stream;          /* cudaStream_t (NULL = legacy default stream)                    */
 } hisq_solve_opts;
 
@@ -154,7 +155,8 @@ typedef struct {
     double seconds;          /* wall time of the call                                         */
     long dslash_calls;       /* Dslash applications (all precisions)                          */
     double dslash_ms;        /* summed event time of the timed sloppy Dslash launches         */
-    long dslash_timed;       /* number of timed launches (profile = 1)                        */
+    long dslash_timed;       /* number of timed launches (profile = 1): dslash_ms / dslash_timed
+                                is the average duration of one sloppy Dslash launch          */
     double bytes_moved;      /* algorithmic bytes of the sloppy Dslash applications           */
     long kernels;            /* kernel launches issued by the call (graph nodes included)     */
 } hisq_stats;

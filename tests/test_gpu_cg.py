@@ -116,7 +116,8 @@ def test_profiled_solve_counts_dslash_launches():
     x = torch.zeros_like(b)
     rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, profile=1, check_interval=10)
     assert rc == hisq.OK
-    assert st.dslash_timed == 2 * st.iterations and st.dslash_ms > 0
+    # one sampled iteration (two Dslash launches) per block of 10 iterations
+    assert st.dslash_timed == 2 * ((st.iterations + 9) // 10) and st.dslash_ms > 0
 
 
 def test_not_converged_and_nan_source():
