@@ -128,6 +128,20 @@ int hisq_dslash_field(hisq_ctx *ctx, int out_parity, const hisq_field *in, hisq_
 int hisq_mdagm(hisq_ctx *ctx, double m, const double *in, double *out, int nrhs, int prec,
                void *stream);
 
+/* out = (4 m^2 - D_eo D_oe) in in FP64, exactly as hisq_mdagm(..., HISQ_F64, ...), but the
+ * call allocates no device memory.  The paper has no counterpart: this entry point exists
+ * for callers that cannot let a library allocate, such as applications whose device memory
+ * belongs to another allocator or a fixed budget, and loops that must not call cudaMalloc
+ * or cudaFree because those calls synchronise the whole device.
+ * The odd-parity intermediate lives in a fixed device array of 1048576 half-lattice sites
+ * (48 MiB) that every GPU loading the library holds until the process exits: nrhs * Vh
+ * above 1048576 returns HISQ_EINVAL.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * share the array: calls that can overlap on the GPU (different streams, or other threads)
+ * race on it and must be serialised by the caller.  in/out: canonical complex128
+ * [nrhs][Vh][3] device buffers, no overlap; stream-ordered on `stream`. */
+int hisq_mdagm_noalloc(hisq_ctx *ctx, double m, const double *in, double *out, int nrhs, void *stream);
+
 /* ------------------------------------------------------------------ solvers */
 typedef struct {
     double tol;            /* target |b - A x| / |b| (recomputed in FP64), e.g. 1e-10       */

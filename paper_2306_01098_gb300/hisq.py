@@ -71,6 +71,7 @@ _SIGS = {
     "hisq_dslash": (_I, [_P, _I, _P, _P, _I, _I, _P]),
     "hisq_dslash_field": (_I, [_P, _I, _P, _P, _P]),
     "hisq_mdagm": (_I, [_P, _D, _P, _P, _I, _I, _P]),
+    "hisq_mdagm_noalloc": (_I, [_P, _D, _P, _P, _I, _P]),
     "hisq_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "hisq_cg": (_I, [_P, _D, _P, _P, _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
     "hisq_multishift_cg": (_I, [_P, _D, _I, _P, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
@@ -158,6 +159,11 @@ class Context:
     def mdagm(self, m, inp, out, prec=F64, stream=None):
         nrhs = inp.numel() // (self.Vh * 3)
         return self.check(lib().hisq_mdagm(self.h, float(m), _ptr(inp), _ptr(out), nrhs, prec, _stream(stream)))
+
+    def mdagm_noalloc(self, m, inp, out, stream=None):
+        """FP64 normal operator without device allocation (fixed scratch array)."""
+        nrhs = inp.numel() // (self.Vh * 3)
+        return self.check(lib().hisq_mdagm_noalloc(self.h, float(m), _ptr(inp), _ptr(out), nrhs, _stream(stream)))
 
     def field(self, prec, nrhs=1):
         return Field(self, prec, nrhs)
