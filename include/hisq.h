@@ -54,7 +54,8 @@ enum hisq_prec {
                       48-bit significand, 8 bytes), float-float arithmetic on the FP32 pipes  */
     HISQ_F32 = 2,  /* float storage and arithmetic                                             */
     HISQ_F16 = 3,  /* half storage (spinors: one float scale per site; links: one float scale
-                      per link type), float arithmetic                                         */
+                      per link type), float arithmetic.  As a solver's sloppy precision: half
+                      links with FP32 iteration vectors                                       */
     HISQ_BF16 = 4, /* as HISQ_F16 with bfloat16 storage                                        */
     HISQ_NPREC = 5
 };
@@ -73,6 +74,9 @@ typedef struct {
                                   per link type such that L/c is in SU(3) (checked at create,
                                   HISQ_EINVAL otherwise) and rebuilds the third row from them  */
     int device;                /* CUDA device ordinal                                            */
+    int autotune;              /* 1 (default): time the Dslash launch shapes (right-hand sides
+                                  per thread, threads per site) on first use of each precision
+                                  and right-hand-side count; 0: size-based defaults             */
 } hisq_opts;
 
 /* Fill `opts` with the defaults (host links, unphased, F64|F64X|F32|F16, 18 reals, device 0). */
@@ -113,13 +117,15 @@ size_t hisq_field_bytes(const hisq_field *f);
 /* ------------------------------------------------------------------ operators */
 /* out = D_{p,1-p} in (Sec. 5.1 stencil; p = out_parity).  `in` holds parity 1-p, `out`
  * receives parity p, both canonical complex128 [nrhs][Vh][3] DEVICE buffers that must not
- * overlap.  `prec` selects the arithmetic/storage of the applied operator; for prec !=
- * HISQ_F64 the vectors are converted to that precision on the way in and back to double on
- * the way out.  Returns HISQ_ENOTBUILT if the context lacks that precision. */
+ * overlap.  `prec` selects the link storage and arithmetic of the applied operator; for
+ * prec != HISQ_F64 the vectors are converted on the way in (F64X: float pairs; F32, F16,
+ * BF16: FP32) and back to double on the way out.  The 16-bit spinor format is applied
+ * through hisq_dslash_field.  Returns HISQ_ENOTBUILT if the context lacks that precision. */
 int hisq_dslash(hisq_ctx *ctx, int out_parity, const double *in, double *out, int nrhs, int prec,
                 void *stream);
 
-/* out = D_{p,1-p} in on internal fields of the same precision and nrhs (no conversions). */
+/* out = D_{p,1-p} in on internal fields of the same precision and nrhs (no conversions);
+ * the field precision is both the link and the vector precision. */
 int hisq_dslash_field(hisq_ctx *ctx, int out_parity, const hisq_field *in, hisq_field *out,
                       void *stream);
 
@@ -141,6 +147,13 @@ int hisq_mdagm(hisq_ctx *ctx, double m, const double *in, double *out, int nrhs,
  * race on it and must be serialised by the caller.  in/out: canonical complex128
  * [nrhs][Vh][3] device buffers, no overlap; stream-ordered on `stream`. */
 int hisq_mdagm_noalloc(hisq_ctx *ctx, double m, const double *in, double *out, int nrhs, void *stream);
+
+/* Fix the Dslash launch shape for (link precision, vector precision, nrhs) instead of the
+ * autotuner's choice: n_inner right-hand sides per thread (1, 2, 4, 8; at most 4 for F64 and
+ * F64X; must divide nrhs) and threads_per_site (1, 2, 4: the four directions are split over
+ * that many threads).  Vector precision equals the link precision, or is HISQ_F32 with
+ * 16-bit links.  Results do not depend on the shape beyond rounding order. */
+int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int n_inner, int threads_per_site);
 
 /* ------------------------------------------------------------------ solvers */
 typedef struct {

@@ -208,6 +208,12 @@ template <> struct Prec<HISQ_F64> {
     }
     static constexpr bool kSplitDirections = false;
     __device__ static void add_acc(Acc &, const Acc &) {}
+    // a += the same accumulator of lane (lane ^ off)
+    __device__ static void shfl_xor_add(Acc &a, int off)
+    {
+#pragma unroll
+        for (int i = 0; i < 6; i++) a.v[i] += __shfl_xor_sync(0xffffffffu, a.v[i], off);
+    }
     // Re <p, o>
     __device__ static double dot(const Vec &p, const Acc &o)
     {
@@ -274,6 +280,12 @@ struct FloatArith {
     }
     static constexpr bool kSplitDirections = false;
     __device__ static void add_acc(Acc &, const Acc &) {}
+    // a += the same accumulator of lane (lane ^ off)
+    __device__ static void shfl_xor_add(Acc &a, int off)
+    {
+#pragma unroll
+        for (int i = 0; i < 6; i++) a.v[i] += __shfl_xor_sync(0xffffffffu, a.v[i], off);
+    }
     __device__ static void mdagm_epilogue(Acc &o, double m4, const Vec &p)
     {
         const float m = (float)m4;
@@ -446,6 +458,14 @@ template <> struct Prec<HISQ_F64X> {
     {
 #pragma unroll
         for (int c = 0; c < 6; c++) dd_add(a.v[c], b.v[c]);
+    }
+    __device__ static void shfl_xor_add(Acc &a, int off)
+    {
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            const DAcc b = {__shfl_xor_sync(0xffffffffu, a.v[c].h, off), __shfl_xor_sync(0xffffffffu, a.v[c].e, off)};
+            dd_add(a.v[c], b);
+        }
     }
     __device__ static void rebuild(Link &, bool) {}
     __device__ static void axpy_acc(Acc &, double, const Acc &) {}

@@ -26,7 +26,7 @@
 namespace hisq {
 
 int apply_mdagm(hisq_ctx *ctx, int prec, double m, const void *in, void *tmp, void *out, int nrhs, size_t rhs_bytes,
-                cudaStream_t st, const Reduce *red);
+                cudaStream_t st, const Reduce *red, bool tune);
 
 // ---------------------------------------------------------------- scalar bookkeeping
 enum { SC_INIT_BB = 0, SC_INIT_R = 1, SC_RU = 2 };
@@ -176,10 +176,11 @@ int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out)
     SolverWork &W = *w;
     W.nrhs = nrhs;
     W.ps = ps;
-    W.px = accum_prec(ps);
+    W.pv = vector_prec(ps);
+    W.px = accum_prec(W.pv);
     W.pp = pp;
     W.Vh = ctx->g.Vh;
-    W.rbS = (size_t)ctx->g.VhPad * spinor_bytes(ps);
+    W.rbS = (size_t)ctx->g.VhPad * spinor_bytes(W.pv);
     W.rbX = (size_t)ctx->g.VhPad * spinor_bytes(W.px);
     W.rb64 = (size_t)ctx->g.Vh * 48;
     W.rbP = (size_t)ctx->g.VhPad * 48;
@@ -231,11 +232,11 @@ void release_work(hisq_ctx *ctx)
 static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, cudaEvent_t *evs)
 {
     const LinkStore &L = ctx->links[w.ps];
-    const int nr = pick_inner(w.ps, w.nrhs);
+    const int nr = w.shape.nr;
     DslashArgs a = make_dslash_args(ctx, w.ps, 1, w.p, w.t, w.nrhs, w.rbS);
     a.skip = w.sc;
     if (evs) cudaEventRecordWithFlags(evs[0], st, cudaEventRecordExternal);
-    cudaError_t e = dslash_launch(w.ps, 0, a, L.nreal, nr, st);
+    cudaError_t e = dslash_launch(w.ps, w.pv, 0, a, L.nreal, w.shape, st);
     if (evs) cudaEventRecordWithFlags(evs[1], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return cuda_error(ctx, e, "sloppy dslash");
     DslashArgs b = make_dslash_args(ctx, w.ps, 0, w.t, w.Ap, w.nrhs, w.rbS);
@@ -245,7 +246,7 @@ static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream
     const int gx = w.nblk_dslash;
     b.red = w.red(FIN_ALPHA, gx, gx * (w.nrhs / nr));
     if (evs) cudaEventRecordWithFlags(evs[2], st, cudaEventRecordExternal);
-    e = dslash_launch(w.ps, 1, b, L.nreal, nr, st);
+    e = dslash_launch(w.ps, w.pv, 1, b, L.nreal, w.shape, st);
     if (evs) cudaEventRecordWithFlags(evs[3], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return cuda_error(ctx, e, "sloppy dslash + epilogue");
     return HISQ_OK;
@@ -258,7 +259,7 @@ static int launch_block(hisq_ctx *ctx, SolverWork &w, double m, int n, cudaStrea
     for (int i = 0; i < n; i++) {
         int rc = sloppy_dslash_pair(ctx, w, m, st, (prof && i == 0) ? &w.prof[0] : nullptr);
         if (rc) return rc;
-        dispatch(w.ps, [&](auto T) {
+        dispatch(w.pv, [&](auto T) {
             decltype(T)::update_r(w, st);
             decltype(T)::update_xp(w, i == n - 1 ? 1 : 0, st);
         });
@@ -273,12 +274,12 @@ int precise_residual(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st)
     int rc;
     const dim3 g(w.nblk_vec, w.nrhs);
     if (w.pp == HISQ_F64) {
-        if ((rc = apply_mdagm(ctx, HISQ_F64, m, w.x64, w.thi, w.Axhi, w.nrhs, w.rb64, st, nullptr))) return rc;
+        if ((rc = apply_mdagm(ctx, HISQ_F64, m, w.x64, w.thi, w.Axhi, w.nrhs, w.rb64, st, nullptr, true))) return rc;
         k_residual<HISQ_F64><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axhi, w.rb64}, VecRef{w.rhi, w.rb64},
                                                      w.Vh, w.red(FIN_STORE, w.nblk_vec));
     } else {
         k_convert<HISQ_F64, HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.x64, w.rb64}, VecRef{w.xx, w.rbP}, w.Vh);
-        if ((rc = apply_mdagm(ctx, HISQ_F64X, m, w.xx, w.tx, w.Axx, w.nrhs, w.rbP, st, nullptr))) return rc;
+        if ((rc = apply_mdagm(ctx, HISQ_F64X, m, w.xx, w.tx, w.Axx, w.nrhs, w.rbP, st, nullptr, true))) return rc;
         k_residual<HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axx, w.rbP}, VecRef{w.rhi, w.rb64},
                                                       w.Vh, w.red(FIN_STORE, w.nblk_vec));
     }
@@ -330,12 +331,14 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         return rc;
     }
     k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_INIT_R, tol2, delta2);
-    dispatch(ps, [&](auto T) {
+    dispatch(w.pv, [&](auto T) {
         decltype(T)::from_hi(w, w.r, st);
         decltype(T)::from_hi(w, w.p, st);
     });
     HISQ_CUDA(ctx, cudaGetLastError());
 
+    // before any capture: the shape (timed on the solver's buffers the first time)
+    w.shape = dslash_shape(ctx, ps, w.pv, nrhs, w.p, w.t, w.rbS, st);
     const int ci = std::max(1, o.check_interval);
     const int interval = ps == HISQ_F64 ? (1 << 30) : std::max(1, o.reliable_interval);
     const bool prof = o.profile != 0;
@@ -409,10 +412,10 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         }
         const bool last = total >= o.maxiter;
         if (any_flag || since_ru >= interval || !any_active || last) {
-            dispatch(ps, [&](auto T) { decltype(T)::accum_hi(w, st); });
+            dispatch(w.pv, [&](auto T) { decltype(T)::accum_hi(w, st); });
             if ((rc = precise_residual(ctx, w, m, st))) return rc;
             k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_RU, tol2, delta2);
-            dispatch(ps, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
+            dispatch(w.pv, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
             kernels += 5 + (w.pp == HISQ_F64X ? 1 : 0);
             nru++;
             since_ru = 0;
@@ -421,7 +424,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             for (int r = 0; r < nrhs; r++) any |= w.h_sc[r].active != 0;
             if (!any || last) break;
         }
-        dispatch(ps, [&](auto T) { decltype(T)::update_xp(w, 2, st); });
+        dispatch(w.pv, [&](auto T) { decltype(T)::update_xp(w, 2, st); });
         kernels++;
     }
     // every exit from the loop follows a reliable update (or no iteration at all), so
@@ -455,7 +458,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         stats->dslash_ms = dms;
         stats->dslash_timed = dtimed;
         const LinkStore &L = ctx->links[ps];
-        const double dsl = (double)w.Vh * (16.0 * link_bytes(ps, L.nreal) + 2.0 * nrhs * spinor_bytes(ps));
+        const double dsl = (double)w.Vh * (16.0 * link_bytes(ps, L.nreal) + 2.0 * nrhs * spinor_bytes(w.pv));
         stats->bytes_moved = 2.0 * iters * dsl;
         stats->kernels = kernels;
     }

@@ -290,6 +290,7 @@ void hisq_opts_default(hisq_opts *o)
     std::memset(o, 0, sizeof(*o));
     o->prec_mask = (1u << HISQ_F64) | (1u << HISQ_F64X) | (1u << HISQ_F32) | (1u << HISQ_F16);
     for (int i = 0; i < HISQ_NPREC; i++) o->compression[i] = 18;
+    o->autotune = 1;
 }
 
 const char *hisq_strerror(int s)
@@ -352,6 +353,7 @@ int hisq_create(hisq_ctx **out, const int dims[4], const double *fat, const doub
     hisq_ctx *ctx = new hisq_ctx();
     ctx->device = opts.device;
     ctx->links_phased = opts.links_phased;
+    ctx->autotune = opts.autotune;
     for (int i = 0; i < 4; i++) ctx->dims[i] = dims[i];
     cudaError_t e = cudaSetDevice(opts.device);
     if (e != cudaSuccess) {

@@ -1,10 +1,14 @@
-// dslash.cu -- precision dispatch and launch of the HISQ Dslash (kernel in dslash_kernel.cuh).
+// dslash.cu -- precision dispatch, launch-shape autotuner and plain launches of the HISQ
+// Dslash (kernels in dslash_kernel.cuh, one translation unit per link/vector precision).
+#include <algorithm>
+#include <vector>
+
 #include "dslash.cuh"
 
 namespace hisq {
 
-// largest N_inner in {8,4,2,1} dividing nrhs (N_inner <= 8; the paper finds spills beyond ~6
-// on its hardware; registers on this GPU allow 8 for 32-bit storage)
+// largest N_inner in {8,4,2,1} dividing nrhs (the paper finds register spills beyond ~6 on
+// its hardware; 32-bit vectors fit 8 here, double-class vectors 4)
 int pick_inner(int prec, int nrhs)
 {
     const int cap = (prec == HISQ_F64 || prec == HISQ_F64X) ? 4 : 8;
@@ -13,14 +17,21 @@ int pick_inner(int prec, int nrhs)
     return 1;
 }
 
-cudaError_t dslash_launch(int prec, int epi, const DslashArgs &a, int nreal, int nr, cudaStream_t st)
+cudaError_t dslash_launch(int pl, int pv, int epi, const DslashArgs &a, int nreal, const DslashShape &sh,
+                          cudaStream_t st)
 {
-    switch (prec) {
-    case HISQ_F64: return dslash_launch_HISQ_F64(epi, a, nreal, nr, st);
-    case HISQ_F64X: return dslash_launch_HISQ_F64X(epi, a, nreal, nr, st);
-    case HISQ_F32: return dslash_launch_HISQ_F32(epi, a, nreal, nr, st);
-    case HISQ_F16: return dslash_launch_HISQ_F16(epi, a, nreal, nr, st);
-    case HISQ_BF16: return dslash_launch_HISQ_BF16(epi, a, nreal, nr, st);
+    const int nr = sh.nr, ds = sh.ds;
+    if (pl == pv) {
+        switch (pl) {
+        case HISQ_F64: return dslash_launch_HISQ_F64_HISQ_F64(epi, a, nreal, nr, ds, st);
+        case HISQ_F64X: return dslash_launch_HISQ_F64X_HISQ_F64X(epi, a, nreal, nr, ds, st);
+        case HISQ_F32: return dslash_launch_HISQ_F32_HISQ_F32(epi, a, nreal, nr, ds, st);
+        case HISQ_F16: return dslash_launch_HISQ_F16_HISQ_F16(epi, a, nreal, nr, ds, st);
+        case HISQ_BF16: return dslash_launch_HISQ_BF16_HISQ_BF16(epi, a, nreal, nr, ds, st);
+        }
+    } else if (pv == HISQ_F32) {
+        if (pl == HISQ_F16) return dslash_launch_HISQ_F16_HISQ_F32(epi, a, nreal, nr, ds, st);
+        if (pl == HISQ_BF16) return dslash_launch_HISQ_BF16_HISQ_F32(epi, a, nreal, nr, ds, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -43,15 +54,104 @@ DslashArgs make_dslash_args(hisq_ctx *ctx, int prec, int out_parity, const void 
     return a;
 }
 
-int launch_dslash(hisq_ctx *ctx, int prec, int out_parity, const void *in, void *out, int nrhs, size_t rhs_bytes,
-                  cudaStream_t st)
+static DslashShape default_shape(hisq_ctx *ctx, int pv, int nrhs)
 {
-    const LinkStore &L = ctx->links[prec];
-    DslashArgs a = make_dslash_args(ctx, prec, out_parity, in, out, nrhs, rhs_bytes);
-    const int nr = pick_inner(prec, nrhs);
-    cudaError_t e = dslash_launch(prec, 0, a, L.nreal, nr, st);
+    DslashShape s;
+    s.nr = pick_inner(pv, nrhs);
+    s.ds = ctx->g.Vh < (1u << 20) ? 2 : 1;
+    return s;
+}
+
+// Autotuner: every (N_inner, threads-per-site) shape that divides the work is timed on the
+// caller's buffers (3 launches after one warm-up, CUDA events on the caller's stream) the
+// first time a key is seen; the fastest is kept for the context's lifetime.
+DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in, void *out, size_t rhs_bytes,
+                         cudaStream_t st)
+{
+    const int key = (pl * 8 + pv) * 256 + nrhs;
+    auto it = ctx->tune.find(key);
+    if (it != ctx->tune.end()) return it->second;
+    DslashShape best = default_shape(ctx, pv, nrhs);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return best;
+    if (!ctx->autotune) {
+        ctx->tune[key] = best;
+        return best;
+    }
+    const int nreal = ctx->links[pl].nreal;
+    const int cap = (pv == HISQ_F64 || pv == HISQ_F64X) ? 4 : 8;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return best;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return best;
+    }
+    DslashArgs a = make_dslash_args(ctx, pl, 0, in, out, nrhs, rhs_bytes);
+    float best_ms = 1e30f;
+    for (int nr = 1; nr <= cap; nr <<= 1) {
+        if (nrhs % nr) continue;
+        for (int ds = 1; ds <= 4; ds <<= 1) {
+            DslashShape sh{nr, ds};
+            if (dslash_launch(pl, pv, 0, a, nreal, sh, st) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(e0, st);
+            for (int i = 0; i < 3; i++) dslash_launch(pl, pv, 0, a, nreal, sh, st);
+            cudaEventRecord(e1, st);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = sh;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tune[key] = best;
+    return best;
+}
+
+int launch_dslash2(hisq_ctx *ctx, int pl, int pv, int out_parity, const void *in, void *out, int nrhs, size_t rhs_bytes,
+                   cudaStream_t st)
+{
+    const LinkStore &L = ctx->links[pl];
+    const DslashShape sh = dslash_shape(ctx, pl, pv, nrhs, in, out, rhs_bytes, st);
+    DslashArgs a = make_dslash_args(ctx, pl, out_parity, in, out, nrhs, rhs_bytes);
+    cudaError_t e = dslash_launch(pl, pv, 0, a, L.nreal, sh, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "dslash launch");
     return HISQ_OK;
 }
+
+int launch_dslash(hisq_ctx *ctx, int prec, int out_parity, const void *in, void *out, int nrhs, size_t rhs_bytes,
+                  cudaStream_t st)
+{
+    return launch_dslash2(ctx, prec, prec, out_parity, in, out, nrhs, rhs_bytes, st);
+}
+
+}  // namespace hisq
+
+using namespace hisq;
+
+extern "C" int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int n_inner,
+                             int threads_per_site)
+{
+    if (!ctx) return HISQ_EINVAL;
+    const bool pair_ok = prec_links >= 0 && prec_links < HISQ_NPREC &&
+                         (prec_vectors == prec_links || (prec_vectors == HISQ_F32 && (prec_links == HISQ_F16 ||
+                                                                                       prec_links == HISQ_BF16)));
+    const int cap = (prec_vectors == HISQ_F64 || prec_vectors == HISQ_F64X) ? 4 : 8;
+    if (!pair_ok || nrhs < 1 || nrhs > 255 || (n_inner != 1 && n_inner != 2 && n_inner != 4 && n_inner != 8) ||
+        n_inner > cap || nrhs % n_inner || (threads_per_site != 1 && threads_per_site != 2 && threads_per_site != 4))
+        return set_error(ctx, HISQ_EINVAL, "hisq_tune_set: bad shape");
+    ctx->tune[(prec_links * 8 + prec_vectors) * 256 + nrhs] = DslashShape{n_inner, threads_per_site};
+    return HISQ_OK;
+}
+
+namespace hisq {
 
 }  // namespace hisq

@@ -1,4 +1,4 @@
-// dslash.cuh -- arguments and launch entry of the Dslash kernels.
+// dslash.cuh -- arguments, launch entry and tuning of the Dslash kernels.
 #pragma once
 
 #include "internal.cuh"
@@ -27,13 +27,23 @@ struct DslashArgs {
 
 DslashArgs make_dslash_args(hisq_ctx *ctx, int prec, int out_parity, const void *in, void *out, int nrhs,
                             size_t rhs_bytes);
-cudaError_t dslash_launch(int prec, int epi, const DslashArgs &a, int nreal, int nr, cudaStream_t st);
+// pl: link storage precision, pv: vector precision (equal, or 16-bit links with FP32 vectors)
+cudaError_t dslash_launch(int pl, int pv, int epi, const DslashArgs &a, int nreal, const DslashShape &sh,
+                          cudaStream_t st);
+// shape for (pl, pv, nrhs) on this context: measured once per key (autotuner) unless tuning
+// is off or the stream is capturing, then a size-based default
+DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in, void *out, size_t rhs_bytes,
+                         cudaStream_t st);
 int pick_inner(int prec, int nrhs);
 
-cudaError_t dslash_launch_HISQ_F64(int epi, const DslashArgs &a, int nreal, int nr, cudaStream_t st);
-cudaError_t dslash_launch_HISQ_F64X(int epi, const DslashArgs &a, int nreal, int nr, cudaStream_t st);
-cudaError_t dslash_launch_HISQ_F32(int epi, const DslashArgs &a, int nreal, int nr, cudaStream_t st);
-cudaError_t dslash_launch_HISQ_F16(int epi, const DslashArgs &a, int nreal, int nr, cudaStream_t st);
-cudaError_t dslash_launch_HISQ_BF16(int epi, const DslashArgs &a, int nreal, int nr, cudaStream_t st);
+#define HISQ_DSLASH_DECLARE(PL, PV) \
+    cudaError_t dslash_launch_##PL##_##PV(int epi, const DslashArgs &a, int nreal, int nr, int ds, cudaStream_t st);
+HISQ_DSLASH_DECLARE(HISQ_F64, HISQ_F64)
+HISQ_DSLASH_DECLARE(HISQ_F64X, HISQ_F64X)
+HISQ_DSLASH_DECLARE(HISQ_F32, HISQ_F32)
+HISQ_DSLASH_DECLARE(HISQ_F16, HISQ_F16)
+HISQ_DSLASH_DECLARE(HISQ_F16, HISQ_F32)
+HISQ_DSLASH_DECLARE(HISQ_BF16, HISQ_BF16)
+HISQ_DSLASH_DECLARE(HISQ_BF16, HISQ_F32)
 
 }  // namespace hisq

@@ -6,12 +6,18 @@
 // links (18 reals) or applied here (12 reals: rows 0 and 1 carry the sign, row 2 is
 // rebuilt and signed in registers).
 //
-// One thread computes one output site for NR right-hand sides (the paper's N_inner loop,
-// Sec. 5.1), so every link is loaded once per NR vectors; grid.y runs over groups of NR
-// right-hand sides (N_outer), adjacent in launch order so the second group finds the
-// links in L2.  Links stream through with L1-bypassing 16-byte loads (read once per
-// application); neighbour spinors are gathered through L1/L2, where their 16-fold reuse
-// happens.  Optional epilogue (normal operator, Sec. 3.2 applyMdaggM):
+// Work decomposition
+//   * NR right-hand sides per thread (the paper's N_inner loop, Sec. 5.1): every link is
+//     loaded once per NR vectors; grid.y runs over groups of NR right-hand sides (N_outer),
+//     adjacent in launch order so the next group finds the links in L2.
+//   * DS threads per site (1, 2 or 4), each taking 4/DS of the directions; the partial sums
+//     meet through warp shuffles.  On small lattices one thread per site leaves a single
+//     short wave whose duration is the latency of 16 dependent gathers; splitting the
+//     directions multiplies the loads in flight.
+//   * Links (PL) stream through with L1-bypassing 16-byte loads, read once per application;
+//     neighbour spinors (PV) are gathered through L1/L2, where their 16-fold reuse happens.
+//     PL and PV differ only for 16-bit links with FP32 vectors.
+// Optional epilogue (normal operator, Sec. 3.2 applyMdaggM):
 //   out = m4 * p - D in,   and <p, out> reduced in FP64 per right-hand side.
 #pragma once
 
@@ -21,24 +27,35 @@
 
 namespace hisq {
 
-template <int P, int NREAL, int NR, int EPI>
+template <int PL, int PV, int NREAL, int NR, int EPI, int DS>
 __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
 {
-    using T = Prec<P>;
-    constexpr int LB = NREAL == 18 ? LinkBytes<P>::b18 : LinkBytes<P>::b12;
-    constexpr bool TWO = (P == HISQ_F16 || P == HISQ_BF16 || NREAL == 12);
+    using T = Prec<PV>;  // vectors and arithmetic
+    using TL = Prec<PL>; // link storage
+    static_assert(std::is_same<typename T::Link, typename TL::Link>::value, "link and vector arithmetic must agree");
+    constexpr int LB = NREAL == 18 ? LinkBytes<PL>::b18 : LinkBytes<PL>::b12;
+    constexpr bool TWO = (PL == HISQ_F16 || PL == HISQ_BF16 || NREAL == 12);
+    constexpr bool SPLIT = T::kSplitDirections;
+    constexpr int NMU = 4 / DS;
     if (a.skip) { // uniform over the grid: the scalars do not change during the launch
         bool any = false;
         for (int r = 0; r < a.nrhs; r++) any |= a.skip[r].active != 0;
         if (!any) return;
     }
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t s = gt / DS;
+    const int part = (int)(gt % DS);
     const int rhs0 = blockIdx.y * NR;
+    const bool live = s < a.g.Vh;
     double dots[NR];
 #pragma unroll
     for (int r = 0; r < NR; r++) dots[r] = 0.0;
 
-    if (s < a.g.Vh) {
+    typename T::Acc out[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) T::zero(out[r]);
+
+    if (live) {
         const Site c = site_coords(a.g, s, a.p);
         typename T::Acc acc[TWO ? 2 : 1][NR];
 #pragma unroll
@@ -46,9 +63,9 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
 #pragma unroll
             for (int r = 0; r < NR; r++) T::zero(acc[t][r]);
 
-        constexpr bool SPLIT = T::kSplitDirections;
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
+        for (int m = 0; m < NMU; m++) {
+            const int mu = part * NMU + m;
             typename T::Acc dacc[SPLIT ? NR : 1];
             if constexpr (SPLIT) {
 #pragma unroll
@@ -66,7 +83,7 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
                 uint32_t w[LB / 4];
                 load_link_words<LB>(slot, back ? sn : s, w);
                 typename T::Link U;
-                T::template unpack<NREAL>(w, U);
+                TL::template unpack<NREAL>(w, U);
                 if constexpr (NREAL == 12) T::rebuild(U, (eta_neg(c, mu) != 0) ^ (mu == 3 && wrap));
 #pragma unroll
                 for (int r = 0; r < NR; r++) {
@@ -80,29 +97,38 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
             if constexpr (SPLIT) {
 #pragma unroll
                 for (int r = 0; r < NR; r++) {
-                    if (mu == 0) acc[0][r] = dacc[r];
+                    if (m == 0) acc[0][r] = dacc[r];
                     else T::add_acc(acc[0][r], dacc[r]);
                 }
             }
         }
-
 #pragma unroll
         for (int r = 0; r < NR; r++) {
-            typename T::Acc o;
             if constexpr (TWO) {
-                T::zero(o);
-                T::axpy_acc(o, (typename T::Real)a.scale[0], acc[0][r]);
-                T::axpy_acc(o, (typename T::Real)a.scale[1], acc[1][r]);
+                T::axpy_acc(out[r], (typename T::Real)a.scale[0], acc[0][r]);
+                T::axpy_acc(out[r], (typename T::Real)a.scale[1], acc[1][r]);
             } else {
-                o = acc[0][r];
+                out[r] = acc[0][r];
             }
+        }
+    }
+    // partial sums of the DS threads of a site meet in every one of them
+    if constexpr (DS > 1) {
+#pragma unroll
+        for (int off = DS / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int r = 0; r < NR; r++) T::shfl_xor_add(out[r], off);
+    }
+    if (live && part == 0) {
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
             if constexpr (EPI == 1) {
                 typename T::Vec pv;
                 T::load(a.pv + (size_t)(rhs0 + r) * a.rhs_bytes, s, pv);
-                T::mdagm_epilogue(o, a.m4, pv);
-                dots[r] = T::dot(pv, o);
+                T::mdagm_epilogue(out[r], a.m4, pv);
+                dots[r] = T::dot(pv, out[r]);
             }
-            T::store(a.out + (size_t)(rhs0 + r) * a.rhs_bytes, s, o);
+            T::store(a.out + (size_t)(rhs0 + r) * a.rhs_bytes, s, out[r]);
         }
     }
     if constexpr (EPI == 1) {
@@ -116,35 +142,50 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
 }
 
 // ---------------------------------------------------------------- launch table
-template <int P, int NREAL, int EPI>
+template <int PL, int PV, int NREAL, int EPI, int DS>
 static cudaError_t launch_nr(const DslashArgs &a, int nr, cudaStream_t st)
 {
-    dim3 grid((a.g.Vh + kDslashBlock - 1) / kDslashBlock, a.nrhs / nr);
+    dim3 grid((unsigned)(((size_t)a.g.Vh * DS + kDslashBlock - 1) / kDslashBlock), a.nrhs / nr);
     switch (nr) {
-    case 1: k_dslash<P, NREAL, 1, EPI><<<grid, kDslashBlock, 0, st>>>(a); break;
-    case 2: k_dslash<P, NREAL, 2, EPI><<<grid, kDslashBlock, 0, st>>>(a); break;
-    case 4: k_dslash<P, NREAL, 4, EPI><<<grid, kDslashBlock, 0, st>>>(a); break;
-    case 8: k_dslash<P, NREAL, 8, EPI><<<grid, kDslashBlock, 0, st>>>(a); break;
+    case 1: k_dslash<PL, PV, NREAL, 1, EPI, DS><<<grid, kDslashBlock, 0, st>>>(a); break;
+    case 2: k_dslash<PL, PV, NREAL, 2, EPI, DS><<<grid, kDslashBlock, 0, st>>>(a); break;
+    case 4: k_dslash<PL, PV, NREAL, 4, EPI, DS><<<grid, kDslashBlock, 0, st>>>(a); break;
+    case 8:
+        if constexpr (PV == HISQ_F64 || PV == HISQ_F64X) return cudaErrorInvalidValue;
+        else k_dslash<PL, PV, NREAL, 8, EPI, DS><<<grid, kDslashBlock, 0, st>>>(a);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <int P, int EPI>
-static cudaError_t launch_prec(const DslashArgs &a, int nreal, int nr, cudaStream_t st)
+template <int PL, int PV, int NREAL, int EPI>
+static cudaError_t launch_ds(const DslashArgs &a, int nr, int ds, cudaStream_t st)
 {
-    if (nreal == 12) {
-        if constexpr (P == HISQ_F64X) return cudaErrorInvalidValue;
-        else return launch_nr<P, 12, EPI>(a, nr, st);
+    switch (ds) {
+    case 1: return launch_nr<PL, PV, NREAL, EPI, 1>(a, nr, st);
+    case 2: return launch_nr<PL, PV, NREAL, EPI, 2>(a, nr, st);
+    case 4: return launch_nr<PL, PV, NREAL, EPI, 4>(a, nr, st);
     }
-    return launch_nr<P, 18, EPI>(a, nr, st);
+    return cudaErrorInvalidValue;
 }
 
-// instantiate the launcher of one precision (one translation unit per precision)
-#define HISQ_DSLASH_INSTANTIATE(P)                                                               \
-    cudaError_t dslash_launch_##P(int epi, const DslashArgs &a, int nreal, int nr, cudaStream_t st) \
-    {                                                                                            \
-        return epi ? launch_prec<P, 1>(a, nreal, nr, st) : launch_prec<P, 0>(a, nreal, nr, st);   \
+template <int PL, int PV, int EPI>
+static cudaError_t launch_prec(const DslashArgs &a, int nreal, int nr, int ds, cudaStream_t st)
+{
+    if (nreal == 12) {
+        if constexpr (PL == HISQ_F64X) return cudaErrorInvalidValue;
+        else return launch_ds<PL, PV, 12, EPI>(a, nr, ds, st);
+    }
+    return launch_ds<PL, PV, 18, EPI>(a, nr, ds, st);
+}
+
+// instantiate the launcher of one link precision with one vector precision
+#define HISQ_DSLASH_INSTANTIATE(PL, PV)                                                                  \
+    cudaError_t dslash_launch_##PL##_##PV(int epi, const DslashArgs &a, int nreal, int nr, int ds,         \
+                                          cudaStream_t st)                                               \
+    {                                                                                                    \
+        return epi ? launch_prec<PL, PV, 1>(a, nreal, nr, ds, st) : launch_prec<PL, PV, 0>(a, nreal, nr, ds, st); \
     }
 
 }  // namespace hisq

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 
 #include "hisq.h"
@@ -143,6 +144,11 @@ __host__ __device__ inline int link_bytes(int prec, int nreal)
     }
 }
 
+// vector storage used with a link precision by the canonical-layout entry points and the
+// solvers: 16-bit links work on FP32 vectors (16-bit iteration vectors lose A-conjugacy at
+// light masses and stall the solve); the 16-bit spinor format is used through fields
+__host__ __device__ inline int vector_prec(int pl) { return (pl == HISQ_F16 || pl == HISQ_BF16) ? HISQ_F32 : pl; }
+
 __host__ __device__ inline int spinor_bytes(int prec)
 {
     switch (prec) {
@@ -180,6 +186,12 @@ struct DevStatus {
 struct SolverWork;
 struct MsWork;
 
+// Dslash launch shape: right-hand sides per thread (N_inner) and threads per site
+struct DslashShape {
+    int nr = 1;
+    int ds = 1;
+};
+
 }  // namespace hisq
 
 // ---------------------------------------------------------------- context and fields
@@ -189,6 +201,8 @@ struct hisq_ctx {
     int dims[4] = {0, 0, 0, 0};
     hisq::Geom g{};
     int links_phased = 0;
+    int autotune = 1;
+    std::map<int, hisq::DslashShape> tune; // autotuned Dslash shapes
     hisq::LinkStore links[HISQ_NPREC];
     int last_error = 0;
     std::string msg;
@@ -223,6 +237,8 @@ void release_ms_work(hisq_ctx *ctx);
     } while (0)
 
 // launch helpers implemented in the .cu files
+int launch_dslash2(hisq_ctx *ctx, int pl, int pv, int out_parity, const void *in, void *out, int nrhs,
+                   size_t rhs_bytes, cudaStream_t st);
 int launch_dslash(hisq_ctx *ctx, int prec, int out_parity, const void *in, void *out, int nrhs,
                   size_t rhs_bytes, cudaStream_t st);
 int launch_import(hisq_ctx *ctx, int prec, const double *src, void *dst, int nrhs, size_t rhs_bytes,

@@ -39,7 +39,8 @@ struct ShiftState {
 };
 
 struct MsWork {
-    int nshift = 0, ps = -1, px = -1;
+    int nshift = 0, ps = -1, pv = -1, px = -1; // sloppy links, sloppy vectors, accumulator
+    DslashShape shape;
     uint32_t Vh = 0;
     size_t rbS = 0, rbX = 0, rb64 = 0;
     char *r = nullptr, *q = nullptr, *t = nullptr, *p = nullptr, *x = nullptr, *b64 = nullptr;
@@ -230,9 +231,10 @@ static int get_ms_work(hisq_ctx *ctx, int nshift, int ps, MsWork **out)
     MsWork &W = *w;
     W.nshift = nshift;
     W.ps = ps;
-    W.px = (ps == HISQ_F64 || ps == HISQ_F64X) ? ps : HISQ_F32;
+    W.pv = vector_prec(ps);
+    W.px = (W.pv == HISQ_F64 || W.pv == HISQ_F64X) ? W.pv : HISQ_F32;
     W.Vh = ctx->g.Vh;
-    W.rbS = (size_t)ctx->g.VhPad * spinor_bytes(ps);
+    W.rbS = (size_t)ctx->g.VhPad * spinor_bytes(W.pv);
     W.rbX = (size_t)ctx->g.VhPad * spinor_bytes(W.px);
     W.rb64 = (size_t)ctx->g.Vh * 48;
     W.nblk_vec = (int)std::min<long>((W.Vh + kVecBlock - 1) / kVecBlock, 4L * ctx->sm_count);
@@ -271,18 +273,18 @@ static int ms_iteration(hisq_ctx *ctx, MsWork &w, double m4s, cudaStream_t st)
     const LinkStore &L = ctx->links[w.ps];
     DslashArgs a = make_dslash_args(ctx, w.ps, 1, w.p, w.t, 1, w.rbS); // p_0 is shift 0
     a.skip = w.sc;
-    cudaError_t e = dslash_launch(w.ps, 0, a, L.nreal, 1, st);
+    cudaError_t e = dslash_launch(w.ps, w.pv, 0, a, L.nreal, w.shape, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "multishift dslash");
     DslashArgs b = make_dslash_args(ctx, w.ps, 0, w.t, w.q, 1, w.rbS);
     b.skip = w.sc;
     b.pv = w.p;
     b.m4 = m4s;
     b.red = w.red(FIN_ALPHA, w.nblk_dslash, w.nblk_dslash);
-    e = dslash_launch(w.ps, 1, b, L.nreal, 1, st);
+    e = dslash_launch(w.ps, w.pv, 1, b, L.nreal, w.shape, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "multishift dslash + epilogue");
-    ms_dispatch(w.ps, [&](auto T) { decltype(T)::update_r(w, st); });
+    ms_dispatch(w.pv, [&](auto T) { decltype(T)::update_r(w, st); });
     k_shift_scalars<<<1, kMaxShift, 0, st>>>(w.ss, w.sc, w.nshift);
-    ms_dispatch(w.ps, [&](auto T) { decltype(T)::shift_update(w, st); });
+    ms_dispatch(w.pv, [&](auto T) { decltype(T)::shift_update(w, st); });
     return HISQ_OK;
 }
 
@@ -363,8 +365,9 @@ extern "C" int hisq_multishift_cg(hisq_ctx *ctx, double m, int nshift, const dou
     k_norm_f64<<<dim3(w.nblk_vec, 1), kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, w.Vh, w.red(FIN_STORE, w.nblk_vec, w.nblk_vec));
     k_ms_init_scalars<<<1, 1, 0, st>>>(w.sc, tmin * tmin);
     k_shift_init<<<1, kMaxShift, 0, st>>>(w.ss, w.sc, nshift);
-    ms_dispatch(ps, [&](auto T) { decltype(T)::start(w, st); });
+    ms_dispatch(w.pv, [&](auto T) { decltype(T)::start(w, st); });
     HISQ_CUDA(ctx, cudaGetLastError());
+    w.shape = dslash_shape(ctx, ps, w.pv, 1, w.p, w.t, w.rbS, st);
 
     const double m4s = 4.0 * m * m + sigma[order[0]];
     const int ci = std::max(1, o.check_interval);
@@ -383,7 +386,7 @@ extern "C" int hisq_multishift_cg(hisq_ctx *ctx, double m, int nshift, const dou
     const bool bad = w.h_sc[0].bad != 0;
     std::vector<double *> xs(nshift);
     for (int k = 0; k < nshift; k++) xs[k] = x[order[k]];
-    ms_dispatch(ps, [&](auto T) { decltype(T)::finish(w, xs.data(), st); });
+    ms_dispatch(w.pv, [&](auto T) { decltype(T)::finish(w, xs.data(), st); });
     HISQ_CUDA(ctx, cudaStreamSynchronize(st));
     if (bad) return set_error(ctx, HISQ_ENOTCONVERGED, "hisq_multishift_cg: non-finite residual");
 

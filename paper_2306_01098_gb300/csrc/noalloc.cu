@@ -17,7 +17,7 @@
 namespace hisq {
 
 int apply_mdagm(hisq_ctx *ctx, int prec, double m, const void *in, void *tmp, void *out, int nrhs, size_t rhs_bytes,
-                cudaStream_t st, const Reduce *red);
+                cudaStream_t st, const Reduce *red, bool tune);
 
 constexpr size_t kNoAllocScratchSites = size_t(1) << 20; // nrhs * Vh must not exceed this
 constexpr int kNoAllocMaxDevices = 64;
@@ -67,5 +67,5 @@ extern "C" int hisq_mdagm_noalloc(hisq_ctx *ctx, double m, const double *in, dou
     if (rc) return rc;
     // the intermediate covers every site of every right-hand side, so nothing needs clearing
     return apply_mdagm(ctx, HISQ_F64, m, in, scratch, out, nrhs, (size_t)ctx->g.Vh * 48, (cudaStream_t)stream,
-                       nullptr);
+                       nullptr, false);
 }

@@ -8,7 +8,9 @@
 namespace hisq {
 
 struct SolverWork {
-    int nrhs = 0, ps = -1, px = -1, pp = -1;
+    int nrhs = 0, ps = -1, pv = -1, px = -1, pp = -1; // sloppy links, sloppy vectors, accumulator, precise
+    DslashShape shape;
+    bool tuned = false;
     uint32_t Vh = 0;
     size_t rbS = 0, rbX = 0, rb64 = 0, rbP = 0; // bytes per rhs: sloppy, accumulator, canonical F64, padded F64
     char *r = nullptr, *p = nullptr, *Ap = nullptr, *t = nullptr, *xlo = nullptr; // sloppy vectors

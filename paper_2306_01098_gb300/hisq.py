@@ -31,7 +31,7 @@ class HisqError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("links_on_device", ctypes.c_int), ("links_phased", ctypes.c_int),
                 ("prec_mask", ctypes.c_uint), ("compression", ctypes.c_int * NPREC),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -72,6 +72,7 @@ _SIGS = {
     "hisq_dslash_field": (_I, [_P, _I, _P, _P, _P]),
     "hisq_mdagm": (_I, [_P, _D, _P, _P, _I, _I, _P]),
     "hisq_mdagm_noalloc": (_I, [_P, _D, _P, _P, _I, _P]),
+    "hisq_tune_set": (_I, [_P, _I, _I, _I, _I, _I]),
     "hisq_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "hisq_cg": (_I, [_P, _D, _P, _P, _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
     "hisq_multishift_cg": (_I, [_P, _D, _I, _P, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
@@ -116,7 +117,8 @@ def _stream(stream):
 class Context:
     """One lattice with its links prepared on the device (hisq_create)."""
 
-    def __init__(self, dims, fat, lng, precs=(F64, F64X, F32, F16), compression=None, phased=False, device=0):
+    def __init__(self, dims, fat, lng, precs=(F64, F64X, F32, F16), compression=None, phased=False, device=0,
+                 autotune=True):
         L = lib()
         o = Opts()
         L.hisq_opts_default(ctypes.byref(o))
@@ -124,6 +126,7 @@ class Context:
         o.links_phased = int(phased)
         o.prec_mask = sum(1 << p for p in precs)
         o.device = device
+        o.autotune = int(autotune)
         for p, c in (compression or {}).items():
             o.compression[p] = c
         d = (ctypes.c_int * 4)(*dims)
@@ -164,6 +167,9 @@ class Context:
         """FP64 normal operator without device allocation (fixed scratch array)."""
         nrhs = inp.numel() // (self.Vh * 3)
         return self.check(lib().hisq_mdagm_noalloc(self.h, float(m), _ptr(inp), _ptr(out), nrhs, _stream(stream)))
+
+    def tune_set(self, prec_links, prec_vectors, nrhs, n_inner, threads_per_site):
+        return self.check(lib().hisq_tune_set(self.h, prec_links, prec_vectors, nrhs, n_inner, threads_per_site))
 
     def field(self, prec, nrhs=1):
         return Field(self, prec, nrhs)

@@ -118,6 +118,49 @@ def test_dslash_multi_rhs(nrhs, prec):
             assert field_rel(got[r], want[r]) <= 2e-6
 
 
+@pytest.mark.parametrize("prec", [hisq.F64, hisq.F64X, hisq.F32, hisq.F16, hisq.BF16])
+def test_dslash_every_launch_shape(prec):
+    # every (right-hand sides per thread, threads per site) shape gives the same operator
+    dims, nrhs = (6, 4, 4, 8), 8
+    ctx, fat, lng = setup(dims)
+    x = fields.gaussian_source(dims, 170, nrhs)
+    want = oracle.dslash(dims, fat, lng, x, 0)
+    pv = hisq.F32 if prec in (hisq.F16, hisq.BF16) else prec
+    tol = {hisq.F32: 2e-6, hisq.F16: 3e-3, hisq.BF16: 2.5e-2}.get(prec)
+    for nr in (1, 2, 4, 8):
+        if nr == 8 and prec in (hisq.F64, hisq.F64X):
+            continue
+        for ds in (1, 2, 4):
+            ctx.tune_set(prec, pv, nrhs, nr, ds)
+            out = torch.full_like(x, float("nan")).cuda()
+            ctx.dslash(0, x.cuda(), out, prec=prec)
+            got = out.cpu().numpy()
+            for r in range(nrhs):
+                if tol is None:
+                    assert site_rel(got[r], want[r]) <= 1e-13, (nr, ds, r)
+                else:
+                    assert field_rel(got[r], want[r]) <= tol, (nr, ds, r)
+    _cache.clear()
+
+
+@pytest.mark.parametrize("prec,tol", [(hisq.F16, 3e-3), (hisq.BF16, 2.5e-2)])
+def test_dslash_16bit_fields(prec, tol):
+    # 16-bit links and 16-bit spinors (one float scale per site) through internal fields
+    dims = (8, 6, 4, 6)
+    ctx, fat, lng = setup(dims)
+    for p in (0, 1):
+        x = fields.gaussian_source(dims, 180 + p, 2)
+        fi, fo = ctx.field(prec, 2), ctx.field(prec, 2)
+        fi.load(x.cuda())
+        ctx.dslash_field(p, fi, fo)
+        out = torch.empty_like(x).cuda()
+        fo.store(out)
+        want = oracle.dslash(dims, fat, lng, x, p)
+        got = out.cpu().numpy()
+        for r in range(2):
+            assert field_rel(got[r], want[r]) <= tol
+
+
 def test_dslash_prephased_links():
     dims = (8, 6, 4, 6)
     ctx, fat, lng = setup(dims, precs=(hisq.F64, hisq.F32), phased=True)
