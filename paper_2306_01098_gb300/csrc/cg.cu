@@ -185,7 +185,7 @@ int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out)
     W.rb64 = (size_t)ctx->g.Vh * 48;
     W.rbP = (size_t)ctx->g.VhPad * 48;
     W.nblk_vec = (int)std::min<long>((W.Vh + kVecBlock - 1) / kVecBlock, 4L * ctx->sm_count);
-    W.nblk_dslash = (int)((W.Vh + kDslashBlock - 1) / kDslashBlock);
+    W.nblk_dslash = (int)((4ull * W.Vh + kDslashBlock - 1) / kDslashBlock); // blocks at 4 threads per site (upper bound)
     int rc = HISQ_OK;
     auto A = [&](char **p, size_t b) { if (rc == HISQ_OK) rc = W.alloc(ctx, p, b); };
     A(&W.r, W.rbS * nrhs);
@@ -243,7 +243,7 @@ static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream
     b.skip = w.sc;
     b.pv = w.p;
     b.m4 = 4.0 * m * m;
-    const int gx = w.nblk_dslash;
+    const int gx = (int)(((size_t)w.Vh * w.shape.ds + kDslashBlock - 1) / kDslashBlock); // blocks along x
     b.red = w.red(FIN_ALPHA, gx, gx * (w.nrhs / nr));
     if (evs) cudaEventRecordWithFlags(evs[2], st, cudaEventRecordExternal);
     e = dslash_launch(w.ps, w.pv, 1, b, L.nreal, w.shape, st);

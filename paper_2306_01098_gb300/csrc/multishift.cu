@@ -238,7 +238,7 @@ static int get_ms_work(hisq_ctx *ctx, int nshift, int ps, MsWork **out)
     W.rbX = (size_t)ctx->g.VhPad * spinor_bytes(W.px);
     W.rb64 = (size_t)ctx->g.Vh * 48;
     W.nblk_vec = (int)std::min<long>((W.Vh + kVecBlock - 1) / kVecBlock, 4L * ctx->sm_count);
-    W.nblk_dslash = (int)((W.Vh + kDslashBlock - 1) / kDslashBlock);
+    W.nblk_dslash = (int)((4ull * W.Vh + kDslashBlock - 1) / kDslashBlock); // blocks at 4 threads per site (upper bound)
     int rc = HISQ_OK;
     auto A = [&](char **p, size_t b) { if (rc == HISQ_OK) rc = ms_alloc(ctx, W, p, b); };
     A(&W.r, W.rbS);
@@ -279,7 +279,8 @@ static int ms_iteration(hisq_ctx *ctx, MsWork &w, double m4s, cudaStream_t st)
     b.skip = w.sc;
     b.pv = w.p;
     b.m4 = m4s;
-    b.red = w.red(FIN_ALPHA, w.nblk_dslash, w.nblk_dslash);
+    const int gx = (int)(((size_t)w.Vh * w.shape.ds + kDslashBlock - 1) / kDslashBlock); // blocks of this launch
+    b.red = w.red(FIN_ALPHA, gx, gx);
     e = dslash_launch(w.ps, w.pv, 1, b, L.nreal, w.shape, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "multishift dslash + epilogue");
     ms_dispatch(w.pv, [&](auto T) { decltype(T)::update_r(w, st); });
