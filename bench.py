@@ -201,15 +201,19 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
-    def solve(prec, precise=hisq.F64, profile=0, xb=x, bb=b, host=0):
+    precise_default = {"f64": hisq.F64, "f64x": hisq.F64X}[args.precise]
+
+    def solve(prec, precise=None, profile=0, xb=x, bb=b, host=0):
+        precise = precise_default if precise is None else precise
         rc, st = ctx.cg(MASS, bb, xb, tol=TOL, prec_sloppy=prec, prec_precise=precise, reliable_interval=100,
+                        l2_persist=int(args.l2_persist),
                         reliable_delta=0.1, profile=profile, host_buffers=host, stream=stream)
         if rc != hisq.OK:
             raise RuntimeError(f"solve did not converge: {st.as_dict()}")
         return st
 
     # plain FP64 CG on the same GPU (the comparator), outside the timed region
-    st64 = solve(hisq.F64)
+    st64 = solve(hisq.F64, precise=hisq.F64)
     x64 = x.clone()
     fp64_ms = []
     for _ in range(args.fp64_reps):
@@ -217,7 +221,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st64 = solve(hisq.F64)
+        st64 = solve(hisq.F64, precise=hisq.F64)
         e1.record(stream)
         torch.cuda.synchronize()
         fp64_ms.append(e0.elapsed_time(e1))
@@ -290,9 +294,10 @@ def run_ours(args, world, rank, local):
     line = {
         "metric": METRIC, "value": ms_per_solve, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_solve, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": f"{args.sloppy}+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "32x32x32x8", "sloppy": args.sloppy, "precise": "f64",
+        "vs_baseline": None, "dtype": f"{args.sloppy}+{args.precise}", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "32x32x32x8", "sloppy": args.sloppy, "precise": args.precise,
                    "reliable_interval": 100, "l2": "flushed between timed solves (256 MB write)",
+                   "l2_persist_links": bool(args.l2_persist),
                    "parallelism": f"replicas x{world}"},
         "iterations": st.iterations, "reliable_updates": st.reliable_updates, "true_residual": st.true_residual,
         "error_vs_fp64": err_vs_fp64, "fp64_cg_ms": fp64_ms, "fp64_iterations": st64.iterations,
@@ -317,7 +322,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--sloppy", default="f32", choices=["f32", "f16", "bf16", "f64x"])
+    ap.add_argument("--sloppy", default="f16", choices=["f32", "f16", "bf16", "f64x"])
+    ap.add_argument("--precise", default="f64", choices=["f64", "f64x"])
+    ap.add_argument("--l2-persist", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash-table", action="store_true")

@@ -171,6 +171,10 @@ typedef struct {
     int use_graph;         /* 1: replay iteration blocks as a captured CUDA graph            */
     int profile;           /* 1: time the sloppy Dslash pair of the first iteration of every
                               block of check_interval iterations with CUDA events            */
+    int l2_persist;        /* 1: keep the sloppy link field in L2 during the solve (persisting
+                              access-policy window on the solver's kernels, within this
+                              process's persisting-L2 limit; persisting lines are released
+                              when the call returns)                                         */
     void *stream;          /* cudaStream_t (NULL = legacy default stream)                    */
 } hisq_solve_opts;
 

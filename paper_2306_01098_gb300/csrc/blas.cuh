@@ -248,6 +248,54 @@ __global__ void __launch_bounds__(kVecBlock) k_residual(VecRef b, VecRef Ax, Vec
     grid_reduce<1>(red, mine, 1, rhs, gridDim.y, blockIdx.x);
 }
 
+// <a, b> = sum conj(a) b per right-hand side (complex), reduced with FIN_CDOT
+template <int PV>
+__global__ void __launch_bounds__(kVecBlock) k_cdot(VecRef a, VecRef b, uint32_t Vh, Reduce red)
+{
+    const int rhs = blockIdx.y;
+    double re = 0.0, im = 0.0;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+        typename Blas<PV>::Vec av, bv;
+        vload<PV>(a.rhs(rhs), s, av);
+        vload<PV>(b.rhs(rhs), s, bv);
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const double ar = Blas<PV>::get(av, 2 * i), ai = Blas<PV>::get(av, 2 * i + 1);
+            const double br = Blas<PV>::get(bv, 2 * i), bi = Blas<PV>::get(bv, 2 * i + 1);
+            re += ar * br + ai * bi;
+            im += ar * bi - ai * br;
+        }
+    }
+    double mine[2] = {block_sum(re), block_sum(im)};
+    grid_reduce<2>(red, mine, 2, 2 * rhs, 2 * gridDim.y, blockIdx.x);
+}
+
+// After a reliable update replaced r: remove from p its component along r, then
+// p = r + beta p, i.e. p = (1 - beta <r,p>/|r|^2) r + beta p  (complex coefficient)
+template <int PV>
+__global__ void __launch_bounds__(kVecBlock) k_p_reortho(VecRef p, VecRef r, uint32_t Vh, const Scalars *sc)
+{
+    const int rhs = blockIdx.y;
+    const Scalars &S = sc[rhs];
+    if (!S.active) return;
+    const double beta = S.beta, rr = S.rr;
+    const double cre = rr > 0.0 ? 1.0 - beta * S.last / rr : 1.0;
+    const double cim = rr > 0.0 ? -beta * S.last_im / rr : 0.0;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+        typename Blas<PV>::Vec pv, rv, out;
+        vload<PV>(p.rhs(rhs), s, pv);
+        vload<PV>(r.rhs(rhs), s, rv);
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const double xr = Blas<PV>::get(rv, 2 * i), xi = Blas<PV>::get(rv, 2 * i + 1);
+            const double yr = Blas<PV>::get(pv, 2 * i), yi = Blas<PV>::get(pv, 2 * i + 1);
+            Blas<PV>::set(out, 2 * i, cre * xr - cim * xi + beta * yr);
+            Blas<PV>::set(out, 2 * i + 1, cre * xi + cim * xr + beta * yi);
+        }
+        Blas<PV>::store(p.rhs(rhs), s, out);
+    }
+}
+
 // |x|^2 (F64) reduced with FIN_STORE
 static __global__ void __launch_bounds__(kVecBlock) k_norm_f64(VecRef x, uint32_t Vh, Reduce red)
 {

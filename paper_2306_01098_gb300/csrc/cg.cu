@@ -51,6 +51,7 @@ __global__ void k_scalars(Scalars *sc, int n, int mode, double tol2, double delt
         S.rr_ref = S.last;
         S.alpha = S.beta = 0.0;
         S.flag = 0;
+        S.paused = 0;
         S.active = (S.last > S.stop) && isfinite(S.last);
         if (!isfinite(S.last)) S.bad = 1;
         break;
@@ -64,13 +65,16 @@ __global__ void k_scalars(Scalars *sc, int n, int mode, double tol2, double delt
             S.active = 0;
             S.beta = 0.0;
         } else {
-            // continuing: beta = |r_true|^2 / |r_old|^2 with |r_old|^2 = rr / beta
-            S.beta = (S.active && S.rr > 0.0) ? S.beta * rt / S.rr : 0.0;
+            // continuing: beta = |r_true|^2 / |r_old|^2 with |r_old|^2 = rr / beta; a right-hand
+            // side that had met the sloppy target restarts from p = r
+            const bool going = S.active || S.paused;
+            S.beta = (going && S.rr > 0.0) ? S.beta * rt / S.rr : 0.0;
             S.active = 1;
         }
         S.rr = rt;
         S.rr_ref = rt;
         S.flag = 0;
+        S.paused = 0;
         break;
     }
     }
@@ -99,6 +103,14 @@ struct Typed {
     static void accum_hi(SolverWork &w, cudaStream_t st)
     {
         k_accum_hi<PX><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.x64, w.rb64}, VecRef{w.xlo, w.rbX}, w.Vh);
+    }
+    // re-orthogonalise p against the replaced residual, then p = r + beta p
+    static void reortho(SolverWork &w, cudaStream_t st)
+    {
+        const dim3 g(w.nblk_vec, w.nrhs);
+        k_cdot<PS><<<g, kVecBlock, 0, st>>>(VecRef{w.r, w.rbS}, VecRef{w.p, w.rbS}, w.Vh,
+                                            w.red(FIN_CDOT, w.nblk_vec, w.nblk_vec * w.nrhs));
+        k_p_reortho<PS><<<g, kVecBlock, 0, st>>>(VecRef{w.p, w.rbS}, VecRef{w.r, w.rbS}, w.Vh, w.sc);
     }
     static void from_hi(SolverWork &w, char *dst, cudaStream_t st)
     {
@@ -294,6 +306,55 @@ static int read_scalars(hisq_ctx *ctx, SolverWork &w, cudaStream_t st)
     return HISQ_OK;
 }
 
+// ---------------------------------------------------------------- L2 residency of the links
+// A persisting access-policy window over the sloppy link store keeps it in L2 across the
+// iterations when it fits (16-bit links of a 32^3 x 8 lattice: 75 MB of the 129 MB L2).
+static cudaAccessPolicyWindow link_window(hisq_ctx *ctx, int ps, bool on)
+{
+    cudaAccessPolicyWindow w{};
+    if (!on) return w;
+    const LinkStore &L = ctx->links[ps];
+    int maxw = 0, maxp = 0;
+    cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device);
+    cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, ctx->device);
+    const size_t bytes = std::min(L.slot_bytes * kSlots, (size_t)maxw);
+    if (maxp <= 0 || bytes == 0) return w;
+    size_t lim = 0;
+    cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize);
+    if (lim < std::min(bytes, (size_t)maxp)) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, std::min(bytes, (size_t)maxp));
+    cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize);
+    w.base_ptr = L.base;
+    w.num_bytes = bytes;
+    w.hitRatio = (float)std::min(1.0, (double)lim / (double)bytes);
+    w.hitProp = cudaAccessPropertyPersisting;
+    w.missProp = cudaAccessPropertyStreaming;
+    return w;
+}
+
+static void set_stream_window(cudaStream_t st, const cudaAccessPolicyWindow &w)
+{
+    cudaStreamAttrValue v{};
+    v.accessPolicyWindow = w;
+    cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v);
+}
+
+// give every kernel node of a captured graph the window (explicitly, not relying on capture)
+static void set_graph_window(cudaGraph_t g, const cudaAccessPolicyWindow &w)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return;
+    cudaKernelNodeAttrValue v{};
+    v.accessPolicyWindow = w;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+            cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributeAccessPolicyWindow, &v);
+    }
+    cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- the solve
 int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const hisq_solve_opts &o, hisq_stats *stats,
            double *residuals)
@@ -339,6 +400,8 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
 
     // before any capture: the shape (timed on the solver's buffers the first time)
     w.shape = dslash_shape(ctx, ps, w.pv, nrhs, w.p, w.t, w.rbS, st);
+    const cudaAccessPolicyWindow win = link_window(ctx, ps, o.l2_persist != 0);
+    set_stream_window(st, win);
     const int ci = std::max(1, o.check_interval);
     const int interval = ps == HISQ_F64 ? (1 << 30) : std::max(1, o.reliable_interval);
     const bool prof = o.profile != 0;
@@ -368,7 +431,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         if (n <= 0) break;
         const bool use_graph = o.use_graph && n == ci;
         if (use_graph) {
-            if (!w.graph || w.graph_n != n || w.graph_m != m || w.graph_prof != prof) {
+            if (!w.graph || w.graph_n != n || w.graph_m != m || w.graph_prof != prof || w.graph_l2 != (win.num_bytes > 0)) {
                 if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
                 cudaGraph_t gr;
                 HISQ_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -376,12 +439,14 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
                 cudaError_t e = cudaStreamEndCapture(st, &gr);
                 if (rc) return rc;
                 if (e != cudaSuccess) return cuda_error(ctx, e, "graph capture");
+                set_graph_window(gr, win);
                 e = cudaGraphInstantiate(&w.graph, gr, 0);
                 cudaGraphDestroy(gr);
                 if (e != cudaSuccess) return cuda_error(ctx, e, "graph instantiate");
                 w.graph_n = n;
                 w.graph_m = m;
                 w.graph_prof = prof;
+                w.graph_l2 = win.num_bytes > 0;
             }
             HISQ_CUDA(ctx, cudaGraphLaunch(w.graph, st));
         } else if ((rc = launch_block(ctx, w, m, n, st, prof))) {
@@ -423,6 +488,9 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             bool any = false;
             for (int r = 0; r < nrhs; r++) any |= w.h_sc[r].active != 0;
             if (!any || last) break;
+            dispatch(w.pv, [&](auto T) { decltype(T)::reortho(w, st); });
+            kernels += 2;
+            continue;
         }
         dispatch(w.pv, [&](auto T) { decltype(T)::update_xp(w, 2, st); });
         kernels++;
@@ -433,6 +501,10 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
     const cudaMemcpyKind k_out = o.host_buffers ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     HISQ_CUDA(ctx, cudaMemcpyAsync(x, w.x64, vb, k_out, st));
     if ((rc = read_scalars(ctx, w, st))) return rc;
+    if (win.num_bytes) { // release the persisting lines and the stream's window
+        set_stream_window(st, cudaAccessPolicyWindow{});
+        cudaCtxResetPersistingL2Cache();
+    }
     // later work on the caller's stream is ordered after the solve
     HISQ_CUDA(ctx, cudaEventRecord(w.ev, st));
     HISQ_CUDA(ctx, cudaStreamWaitEvent(ust, w.ev, 0));

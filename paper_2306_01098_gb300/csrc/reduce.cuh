@@ -26,6 +26,8 @@ struct Scalars {
     int it_all;     // iterations launched (advanced by every |r|^2 reduction)
     int astamp;     // it_all of the iteration whose <p,Ap> produced alpha
     int active;     // 1 while iterating
+    int paused;     // 1: stopped for a reliable update (sloppy residual fell below delta)
+    double last_im; // scratch: imaginary part of the last reduced complex value
     int flag;       // 1: reliable update wanted (sloppy target or delta reached)
     int bad;        // 1: non-finite or non-positive curvature seen
     int pad;
@@ -42,6 +44,7 @@ enum FinishOp {
     FIN_STORE = 0, // last = total
     FIN_ALPHA = 1, // pAp = total; alpha = rr / pAp
     FIN_RR = 2,    // beta = total / rr; rr = total; set flag when below stop / delta
+    FIN_CDOT = 3,  // value 2k -> last, 2k+1 -> last_im of right-hand side k
 };
 
 struct Reduce {
@@ -55,7 +58,7 @@ struct Reduce {
 
 __device__ __forceinline__ void finish_value(const Reduce &R, int v, double total)
 {
-    Scalars &S = R.sc[v];
+    Scalars &S = R.sc[R.op == FIN_CDOT ? (v >> 1) : v];
     switch (R.op) {
     case FIN_ALPHA:
         S.pAp = total;
@@ -78,11 +81,21 @@ __device__ __forceinline__ void finish_value(const Reduce &R, int v, double tota
             }
             S.beta = S.rr > 0.0 ? total / S.rr : 0.0;
             S.rr = total;
-            if (total <= S.stop || total < S.delta2 * S.rr_ref) S.flag = 1;
-            if (total <= S.stop) S.active = 0;
+            // the sloppy residual may not run ahead of the true one: at the target, or a
+            // factor delta below the last recomputed residual, the right-hand side pauses
+            // until the host's reliable update (delta2 = 0 for plain FP64 solves)
+            if (total <= S.stop || total < S.delta2 * S.rr_ref) {
+                S.flag = 1;
+                S.active = 0;
+                S.paused = total > S.stop;
+            }
         } else {
             S.beta = 0.0;
         }
+        break;
+    case FIN_CDOT:
+        if (v & 1) R.sc[v >> 1].last_im = total;
+        else R.sc[v >> 1].last = total;
         break;
     default:
         S.last = total;

@@ -27,6 +27,7 @@ struct SolverWork {
     int graph_n = 0;
     double graph_m = -1.0;
     bool graph_prof = false;
+    bool graph_l2 = false;
     std::vector<cudaEvent_t> prof;
     std::vector<void *> allocs;
 

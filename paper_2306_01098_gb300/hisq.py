@@ -39,7 +39,8 @@ class SolveOpts(ctypes.Structure):
                 ("prec_precise", ctypes.c_int), ("reliable_interval", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("zero_guess", ctypes.c_int),
                 ("host_buffers", ctypes.c_int), ("check_interval", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("use_graph", ctypes.c_int), ("profile", ctypes.c_int), ("l2_persist", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
