@@ -297,7 +297,7 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None, "dtype": f"{args.sloppy}+{args.precise}", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": "32x32x32x8", "sloppy": args.sloppy, "precise": args.precise,
                    "reliable_interval": 100, "l2": "flushed between timed solves (256 MB write)",
-                   "l2_persist_links": bool(args.l2_persist),
+                   "l2_persist_links": {-1: "auto", 0: "off", 1: "on"}[args.l2_persist],
                    "parallelism": f"replicas x{world}"},
         "iterations": st.iterations, "reliable_updates": st.reliable_updates, "true_residual": st.true_residual,
         "error_vs_fp64": err_vs_fp64, "fp64_cg_ms": fp64_ms, "fp64_iterations": st64.iterations,
@@ -324,7 +324,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sloppy", default="f16", choices=["f32", "f16", "bf16", "f64x"])
     ap.add_argument("--precise", default="f64", choices=["f64", "f64x"])
-    ap.add_argument("--l2-persist", type=int, default=0)
+    ap.add_argument("--l2-persist", type=int, default=-1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash-table", action="store_true")

@@ -167,14 +167,17 @@ typedef struct {
     double reliable_delta; /* also update when |r| < delta * |r| at the last update (0.1)    */
     int zero_guess;        /* 1: start from x = 0; 0: x holds the initial guess              */
     int host_buffers;      /* 1: b and x are host pointers (copied inside the call)          */
-    int check_interval;    /* iterations between host-side convergence checks (default 50)   */
-    int use_graph;         /* 1: replay iteration blocks as a captured CUDA graph            */
+    int check_interval;    /* use_graph = 0: iterations per block of direct launches (50)    */
+    int use_graph;         /* 1 (default): iterations run inside a CUDA graph WHILE node
+                              that the device stops when every right-hand side pauses or
+                              converges; the host looks at the scalars once per phase      */
     int profile;           /* 1: time the sloppy Dslash pair of the first iteration of every
                               block of check_interval iterations with CUDA events            */
-    int l2_persist;        /* 1: keep the sloppy link field in L2 during the solve (persisting
+    int l2_persist;        /* keep the sloppy link field in L2 during the solve (persisting
                               access-policy window on the solver's kernels, within this
                               process's persisting-L2 limit; persisting lines are released
-                              when the call returns)                                         */
+                              when the call returns): 1 on, 0 off, -1 (default) when the
+                              whole field fits the device's persisting-L2 maximum          */
     void *stream;          /* cudaStream_t (NULL = legacy default stream)                    */
 } hisq_solve_opts;
 

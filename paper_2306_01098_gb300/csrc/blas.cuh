@@ -161,8 +161,9 @@ __global__ void __launch_bounds__(kVecBlock) k_update_r(VecRef r, VecRef Ap, uin
 // mode 0: x += alpha p, p = r + beta p;  mode 1: x += alpha p;  mode 2: p = r + beta p
 template <int PS, int PX>
 __global__ void __launch_bounds__(kVecBlock) k_update_xp(VecRef x, VecRef p, VecRef r, uint32_t Vh, const Scalars *sc,
-                                                         int mode)
+                                                         int mode, const LoopCtl *ctl)
 {
+    if (ctl) mode = ctl->mode; // inside a device-controlled loop
     using BS = Blas<PS>;
     using BX = Blas<PX>;
     const int rhs = blockIdx.y;

@@ -90,15 +90,17 @@ static int accum_prec(int ps) { return (ps == HISQ_F64 || ps == HISQ_F64X) ? ps 
 // ---------------------------------------------------------------- typed launches
 template <int PS, int PX>
 struct Typed {
-    static void update_r(SolverWork &w, cudaStream_t st)
+    static void update_r(SolverWork &w, cudaStream_t st, LoopCtl *ctl = nullptr, unsigned long long cond = 0)
     {
-        k_update_r<PS><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.r, w.rbS}, VecRef{w.Ap, w.rbS}, w.Vh,
-                                                                       w.red(FIN_RR, w.nblk_vec));
+        Reduce R = w.red(FIN_RR, w.nblk_vec);
+        R.ctl = ctl;
+        R.cond = cond;
+        k_update_r<PS><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.r, w.rbS}, VecRef{w.Ap, w.rbS}, w.Vh, R);
     }
-    static void update_xp(SolverWork &w, int mode, cudaStream_t st)
+    static void update_xp(SolverWork &w, int mode, cudaStream_t st, const LoopCtl *ctl = nullptr)
     {
         k_update_xp<PS, PX><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(
-            VecRef{w.xlo, w.rbX}, VecRef{w.p, w.rbS}, VecRef{w.r, w.rbS}, w.Vh, w.sc, mode);
+            VecRef{w.xlo, w.rbX}, VecRef{w.p, w.rbS}, VecRef{w.r, w.rbS}, w.Vh, w.sc, mode, ctl);
     }
     static void accum_hi(SolverWork &w, cudaStream_t st)
     {
@@ -222,6 +224,8 @@ int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out)
     W.partials = reinterpret_cast<double *>(tmp);
     A(&tmp, 64);
     W.counter = reinterpret_cast<unsigned *>(tmp);
+    A(&tmp, sizeof(LoopCtl));
+    W.ctl = reinterpret_cast<LoopCtl *>(tmp);
     if (rc) return rc;
     if (cudaMallocHost(&W.h_sc, sizeof(Scalars) * (nrhs + 64)) != cudaSuccess) return set_error(ctx, HISQ_ENOMEM, "pinned scalars");
     if (cudaStreamCreateWithFlags(&W.st, cudaStreamNonBlocking) != cudaSuccess ||
@@ -240,85 +244,22 @@ void release_work(hisq_ctx *ctx)
     }
 }
 
-// ---------------------------------------------------------------- pieces of the iteration
-static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, cudaEvent_t *evs)
-{
-    const LinkStore &L = ctx->links[w.ps];
-    const int nr = w.shape.nr;
-    DslashArgs a = make_dslash_args(ctx, w.ps, 1, w.p, w.t, w.nrhs, w.rbS);
-    a.skip = w.sc;
-    if (evs) cudaEventRecordWithFlags(evs[0], st, cudaEventRecordExternal);
-    cudaError_t e = dslash_launch(w.ps, w.pv, 0, a, L.nreal, w.shape, st);
-    if (evs) cudaEventRecordWithFlags(evs[1], st, cudaEventRecordExternal);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "sloppy dslash");
-    DslashArgs b = make_dslash_args(ctx, w.ps, 0, w.t, w.Ap, w.nrhs, w.rbS);
-    b.skip = w.sc;
-    b.pv = w.p;
-    b.m4 = 4.0 * m * m;
-    const int gx = (int)(((size_t)w.Vh * w.shape.ds + kDslashBlock - 1) / kDslashBlock); // blocks along x
-    b.red = w.red(FIN_ALPHA, gx, gx * (w.nrhs / nr));
-    if (evs) cudaEventRecordWithFlags(evs[2], st, cudaEventRecordExternal);
-    e = dslash_launch(w.ps, w.pv, 1, b, L.nreal, w.shape, st);
-    if (evs) cudaEventRecordWithFlags(evs[3], st, cudaEventRecordExternal);
-    if (e != cudaSuccess) return cuda_error(ctx, e, "sloppy dslash + epilogue");
-    return HISQ_OK;
-}
-
-// profile: the two Dslash launches of the first iteration of every block are bracketed by
-// events (a sample of every block, so the timing costs nothing measurable)
-static int launch_block(hisq_ctx *ctx, SolverWork &w, double m, int n, cudaStream_t st, bool prof)
-{
-    for (int i = 0; i < n; i++) {
-        int rc = sloppy_dslash_pair(ctx, w, m, st, (prof && i == 0) ? &w.prof[0] : nullptr);
-        if (rc) return rc;
-        dispatch(w.pv, [&](auto T) {
-            decltype(T)::update_r(w, st);
-            decltype(T)::update_xp(w, i == n - 1 ? 1 : 0, st);
-        });
-    }
-    HISQ_CUDA(ctx, cudaGetLastError());
-    return HISQ_OK;
-}
-
-// r_hi = b - A_precise x_hi ; |r_hi|^2 -> Scalars.last
-int precise_residual(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st)
-{
-    int rc;
-    const dim3 g(w.nblk_vec, w.nrhs);
-    if (w.pp == HISQ_F64) {
-        if ((rc = apply_mdagm(ctx, HISQ_F64, m, w.x64, w.thi, w.Axhi, w.nrhs, w.rb64, st, nullptr, true))) return rc;
-        k_residual<HISQ_F64><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axhi, w.rb64}, VecRef{w.rhi, w.rb64},
-                                                     w.Vh, w.red(FIN_STORE, w.nblk_vec));
-    } else {
-        k_convert<HISQ_F64, HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.x64, w.rb64}, VecRef{w.xx, w.rbP}, w.Vh);
-        if ((rc = apply_mdagm(ctx, HISQ_F64X, m, w.xx, w.tx, w.Axx, w.nrhs, w.rbP, st, nullptr, true))) return rc;
-        k_residual<HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axx, w.rbP}, VecRef{w.rhi, w.rb64},
-                                                      w.Vh, w.red(FIN_STORE, w.nblk_vec));
-    }
-    HISQ_CUDA(ctx, cudaGetLastError());
-    return HISQ_OK;
-}
-
-static int read_scalars(hisq_ctx *ctx, SolverWork &w, cudaStream_t st)
-{
-    HISQ_CUDA(ctx, cudaMemcpyAsync(w.h_sc, w.sc, sizeof(Scalars) * w.nrhs, cudaMemcpyDeviceToHost, st));
-    HISQ_CUDA(ctx, cudaStreamSynchronize(st));
-    return HISQ_OK;
-}
-
 // ---------------------------------------------------------------- L2 residency of the links
 // A persisting access-policy window over the sloppy link store keeps it in L2 across the
 // iterations when it fits (16-bit links of a 32^3 x 8 lattice: 75 MB of the 129 MB L2).
-static cudaAccessPolicyWindow link_window(hisq_ctx *ctx, int ps, bool on)
+// mode: 0 off, 1 on, -1 automatic (on when the whole store fits in the persisting L2 limit)
+static cudaAccessPolicyWindow link_window(hisq_ctx *ctx, int ps, int mode)
 {
     cudaAccessPolicyWindow w{};
-    if (!on) return w;
+    if (mode == 0) return w;
     const LinkStore &L = ctx->links[ps];
     int maxw = 0, maxp = 0;
     cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device);
     cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, ctx->device);
-    const size_t bytes = std::min(L.slot_bytes * kSlots, (size_t)maxw);
+    const size_t store = L.slot_bytes * kSlots;
+    const size_t bytes = std::min(store, (size_t)maxw);
     if (maxp <= 0 || bytes == 0) return w;
+    if (mode < 0 && (store > (size_t)maxp || store > (size_t)maxw)) return w;
     size_t lim = 0;
     cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize);
     if (lim < std::min(bytes, (size_t)maxp)) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, std::min(bytes, (size_t)maxp));
@@ -353,6 +294,117 @@ static void set_graph_window(cudaGraph_t g, const cudaAccessPolicyWindow &w)
             cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributeAccessPolicyWindow, &v);
     }
     cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- pieces of the iteration
+static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, cudaEvent_t *evs)
+{
+    const LinkStore &L = ctx->links[w.ps];
+    const int nr = w.shape.nr;
+    DslashArgs a = make_dslash_args(ctx, w.ps, 1, w.p, w.t, w.nrhs, w.rbS);
+    a.skip = w.sc;
+    if (evs) cudaEventRecordWithFlags(evs[0], st, cudaEventRecordExternal);
+    cudaError_t e = dslash_launch(w.ps, w.pv, 0, a, L.nreal, w.shape, st);
+    if (evs) cudaEventRecordWithFlags(evs[1], st, cudaEventRecordExternal);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "sloppy dslash");
+    DslashArgs b = make_dslash_args(ctx, w.ps, 0, w.t, w.Ap, w.nrhs, w.rbS);
+    b.skip = w.sc;
+    b.pv = w.p;
+    b.m4 = 4.0 * m * m;
+    const int gx = (int)(((size_t)w.Vh * w.shape.ds + kDslashBlock - 1) / kDslashBlock); // blocks along x
+    b.red = w.red(FIN_ALPHA, gx, gx * (w.nrhs / nr));
+    if (evs) cudaEventRecordWithFlags(evs[2], st, cudaEventRecordExternal);
+    e = dslash_launch(w.ps, w.pv, 1, b, L.nreal, w.shape, st);
+    if (evs) cudaEventRecordWithFlags(evs[3], st, cudaEventRecordExternal);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "sloppy dslash + epilogue");
+    return HISQ_OK;
+}
+
+// one iteration: Dslash pair, r update (whose last block also runs the loop control), x/p
+// update (its mode comes from the loop control: p is left alone in a phase's last iteration)
+static int launch_iteration(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, cudaEvent_t *evs,
+                            unsigned long long cond)
+{
+    int rc = sloppy_dslash_pair(ctx, w, m, st, evs);
+    if (rc) return rc;
+    dispatch(w.pv, [&](auto T) {
+        decltype(T)::update_r(w, st, w.ctl, cond);
+        decltype(T)::update_xp(w, 0, st, w.ctl);
+    });
+    HISQ_CUDA(ctx, cudaGetLastError());
+    return HISQ_OK;
+}
+
+__global__ void k_phase_begin(LoopCtl *ctl, const Scalars *sc, int cap)
+{
+    ctl->start = sc[0].it_all;
+    ctl->cap = cap;
+    ctl->mode = 0;
+}
+
+// The iteration loop as a CUDA graph: one WHILE node whose body is one iteration; the
+// r update's finishing block clears the condition when no right-hand side is active or the
+// phase's iteration cap is reached, so the device runs exactly the iterations needed
+static int build_loop_graph(hisq_ctx *ctx, SolverWork &w, double m, const cudaAccessPolicyWindow &win, cudaStream_t st)
+{
+    cudaGraph_t g = nullptr;
+    HISQ_CUDA(ctx, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_error(ctx, e, "conditional graph node");
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_error(ctx, e, "capture into loop body");
+    }
+    int rc = launch_iteration(ctx, w, m, st, nullptr, (unsigned long long)h);
+    e = cudaStreamEndCapture(st, &body);
+    if (rc || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return rc ? rc : cuda_error(ctx, e, "capture into loop body");
+    }
+    set_graph_window(body, win);
+    e = cudaGraphInstantiate(&w.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "loop graph instantiate");
+    return HISQ_OK;
+}
+
+// r_hi = b - A_precise x_hi ; |r_hi|^2 -> Scalars.last
+int precise_residual(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st)
+{
+    int rc;
+    const dim3 g(w.nblk_vec, w.nrhs);
+    if (w.pp == HISQ_F64) {
+        if ((rc = apply_mdagm(ctx, HISQ_F64, m, w.x64, w.thi, w.Axhi, w.nrhs, w.rb64, st, nullptr, true))) return rc;
+        k_residual<HISQ_F64><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axhi, w.rb64}, VecRef{w.rhi, w.rb64},
+                                                     w.Vh, w.red(FIN_STORE, w.nblk_vec));
+    } else {
+        k_convert<HISQ_F64, HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.x64, w.rb64}, VecRef{w.xx, w.rbP}, w.Vh);
+        if ((rc = apply_mdagm(ctx, HISQ_F64X, m, w.xx, w.tx, w.Axx, w.nrhs, w.rbP, st, nullptr, true))) return rc;
+        k_residual<HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axx, w.rbP}, VecRef{w.rhi, w.rb64},
+                                                      w.Vh, w.red(FIN_STORE, w.nblk_vec));
+    }
+    HISQ_CUDA(ctx, cudaGetLastError());
+    return HISQ_OK;
+}
+
+static int read_scalars(hisq_ctx *ctx, SolverWork &w, cudaStream_t st)
+{
+    HISQ_CUDA(ctx, cudaMemcpyAsync(w.h_sc, w.sc, sizeof(Scalars) * w.nrhs, cudaMemcpyDeviceToHost, st));
+    HISQ_CUDA(ctx, cudaStreamSynchronize(st));
+    return HISQ_OK;
 }
 
 // ---------------------------------------------------------------- the solve
@@ -400,7 +452,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
 
     // before any capture: the shape (timed on the solver's buffers the first time)
     w.shape = dslash_shape(ctx, ps, w.pv, nrhs, w.p, w.t, w.rbS, st);
-    const cudaAccessPolicyWindow win = link_window(ctx, ps, o.l2_persist != 0);
+    const cudaAccessPolicyWindow win = link_window(ctx, ps, o.l2_persist);
     set_stream_window(st, win);
     const int ci = std::max(1, o.check_interval);
     const int interval = ps == HISQ_F64 ? (1 << 30) : std::max(1, o.reliable_interval);
@@ -413,7 +465,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         }
         if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
     }
-    int total = 0, since_ru = 0, nru = 0, prev_iters = 0;
+    int since_ru = 0, nru = 0, prev_iters = 0, it_all = 0;
     long kernels = 6 + (o.zero_guess ? 0 : 3); // setup: norms, scalars, conversions (+ residual)
     long dcalls = 0;
     double dms = 0.0;
@@ -425,37 +477,40 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         bool any = false;
         for (int r = 0; r < nrhs; r++) any |= w.h_sc[r].active != 0;
         done = !any;
+        it_all = w.h_sc[0].it_all;
     }
+    const int it_start = it_all;
+    // Phases: a phase runs iterations until every right-hand side pauses or converges, or
+    // until its cap (the next scheduled reliable update, maxiter, or check_interval for
+    // direct launches); then the host looks at the scalars once.
     while (!done) {
-        const int n = std::min(ci, o.maxiter - total);
-        if (n <= 0) break;
-        const bool use_graph = o.use_graph && n == ci;
-        if (use_graph) {
-            if (!w.graph || w.graph_n != n || w.graph_m != m || w.graph_prof != prof || w.graph_l2 != (win.num_bytes > 0)) {
+        const int budget = o.maxiter - (it_all - it_start);
+        if (budget <= 0) break;
+        int cap = std::min(interval - since_ru, budget);
+        if (!o.use_graph) cap = std::min(cap, ci);
+        k_phase_begin<<<1, 1, 0, st>>>(w.ctl, w.sc, cap);
+        kernels++;
+        if (o.use_graph) {
+            if (prof) { // sampled timing: the phase's first iteration runs outside the graph
+                if ((rc = launch_iteration(ctx, w, m, st, &w.prof[0], 0))) return rc;
+                kernels += 4;
+            }
+            if (!w.graph || w.graph_m != m || w.graph_l2 != (win.num_bytes > 0)) {
                 if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
-                cudaGraph_t gr;
-                HISQ_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-                rc = launch_block(ctx, w, m, n, st, prof);
-                cudaError_t e = cudaStreamEndCapture(st, &gr);
-                if (rc) return rc;
-                if (e != cudaSuccess) return cuda_error(ctx, e, "graph capture");
-                set_graph_window(gr, win);
-                e = cudaGraphInstantiate(&w.graph, gr, 0);
-                cudaGraphDestroy(gr);
-                if (e != cudaSuccess) return cuda_error(ctx, e, "graph instantiate");
-                w.graph_n = n;
+                if ((rc = build_loop_graph(ctx, w, m, win, st))) return rc;
                 w.graph_m = m;
-                w.graph_prof = prof;
                 w.graph_l2 = win.num_bytes > 0;
             }
             HISQ_CUDA(ctx, cudaGraphLaunch(w.graph, st));
-        } else if ((rc = launch_block(ctx, w, m, n, st, prof))) {
-            return rc;
+        } else {
+            for (int i = 0; i < cap; i++)
+                if ((rc = launch_iteration(ctx, w, m, st, (prof && i == 0) ? &w.prof[0] : nullptr, 0))) return rc;
         }
-        total += n;
-        since_ru += n;
-        kernels += 4L * n;
         if ((rc = read_scalars(ctx, w, st))) return rc;
+        const int executed = w.h_sc[0].it_all - it_all; // iterations the device ran in this phase
+        it_all = w.h_sc[0].it_all;
+        since_ru += executed;
+        kernels += 4L * executed - (o.use_graph && prof ? 4 : 0);
         int it = 0;
         bool any_active = false, any_flag = false;
         for (int r = 0; r < nrhs; r++) {
@@ -463,7 +518,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             any_active |= w.h_sc[r].active != 0;
             any_flag |= w.h_sc[r].flag != 0;
         }
-        const int ran = it - prev_iters; // iterations that did work in this block
+        const int ran = it - prev_iters; // iterations that did work
         prev_iters = it;
         dcalls += 2L * ran;
         if (prof && ran > 0) {
@@ -475,7 +530,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
                 }
             }
         }
-        const bool last = total >= o.maxiter;
+        const bool last = it_all - it_start >= o.maxiter;
         if (any_flag || since_ru >= interval || !any_active || last) {
             dispatch(w.pv, [&](auto T) { decltype(T)::accum_hi(w, st); });
             if ((rc = precise_residual(ctx, w, m, st))) return rc;
@@ -492,6 +547,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             kernels += 2;
             continue;
         }
+        // the phase ended at its cap with p not yet updated
         dispatch(w.pv, [&](auto T) { decltype(T)::update_xp(w, 2, st); });
         kernels++;
     }
@@ -557,6 +613,7 @@ void hisq_solve_opts_default(hisq_solve_opts *o)
     o->zero_guess = 1;
     o->check_interval = 50;
     o->use_graph = 1;
+    o->l2_persist = -1;
 }
 
 int hisq_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const hisq_solve_opts *opts,

@@ -47,7 +47,18 @@ enum FinishOp {
     FIN_CDOT = 3,  // value 2k -> last, 2k+1 -> last_im of right-hand side k
 };
 
+// iteration control of a device-side solver loop (a CUDA graph WHILE node): the block that
+// finishes the |r|^2 reduction also decides whether the loop goes on
+struct LoopCtl {
+    int start; // it_all when the phase began
+    int cap;   // iterations allowed in this phase
+    int mode;  // for the x/p update of this iteration: 0 = x and p, 1 = x only (last iteration)
+    int pad;
+};
+
 struct Reduce {
+    LoopCtl *ctl = nullptr;               // if set: decide continuation after finishing
+    unsigned long long cond = 0;          // graph conditional handle (0: not inside a graph)
     double *partials = nullptr; // [nval][nblocks]
     unsigned *counter = nullptr;
     Scalars *sc = nullptr;      // nval scalars (indexed from sc_offset)
@@ -149,6 +160,13 @@ __device__ __forceinline__ void grid_reduce(const Reduce &R, const double (&mine
         if (threadIdx.x == 0) finish_value(R, v, x);
     }
     if (threadIdx.x == 0) {
+        if (R.ctl) {
+            bool any = false;
+            for (int v = 0; v < nval_all; v++) any |= R.sc[v].active != 0;
+            const bool last = R.sc[0].it_all - R.ctl->start >= R.ctl->cap;
+            R.ctl->mode = last ? 1 : 0;
+            if (R.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)R.cond, (any && !last) ? 1u : 0u);
+        }
         __threadfence();
         *R.counter = 0u;
     }

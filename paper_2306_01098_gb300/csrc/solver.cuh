@@ -20,13 +20,12 @@ struct SolverWork {
     Scalars *h_sc = nullptr; // pinned host copy
     double *partials = nullptr;
     unsigned *counter = nullptr;
+    LoopCtl *ctl = nullptr;  // device-side loop control
     int nblk_vec = 0, nblk_dslash = 0;
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     cudaGraphExec_t graph = nullptr;
-    int graph_n = 0;
     double graph_m = -1.0;
-    bool graph_prof = false;
     bool graph_l2 = false;
     std::vector<cudaEvent_t> prof;
     std::vector<void *> allocs;
