@@ -303,9 +303,9 @@ static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream
     const int nr = w.shape.nr;
     DslashArgs a = make_dslash_args(ctx, w.ps, 1, w.p, w.t, w.nrhs, w.rbS);
     a.skip = w.sc;
-    if (evs) cudaEventRecordWithFlags(evs[0], st, cudaEventRecordExternal);
+    if (evs) cudaEventRecord(evs[0], st);
     cudaError_t e = dslash_launch(w.ps, w.pv, 0, a, L.nreal, w.shape, st);
-    if (evs) cudaEventRecordWithFlags(evs[1], st, cudaEventRecordExternal);
+    if (evs) cudaEventRecord(evs[1], st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "sloppy dslash");
     DslashArgs b = make_dslash_args(ctx, w.ps, 0, w.t, w.Ap, w.nrhs, w.rbS);
     b.skip = w.sc;
@@ -313,9 +313,9 @@ static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream
     b.m4 = 4.0 * m * m;
     const int gx = (int)(((size_t)w.Vh * w.shape.ds + kDslashBlock - 1) / kDslashBlock); // blocks along x
     b.red = w.red(FIN_ALPHA, gx, gx * (w.nrhs / nr));
-    if (evs) cudaEventRecordWithFlags(evs[2], st, cudaEventRecordExternal);
+    if (evs) cudaEventRecord(evs[2], st);
     e = dslash_launch(w.ps, w.pv, 1, b, L.nreal, w.shape, st);
-    if (evs) cudaEventRecordWithFlags(evs[3], st, cudaEventRecordExternal);
+    if (evs) cudaEventRecord(evs[3], st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "sloppy dslash + epilogue");
     return HISQ_OK;
 }

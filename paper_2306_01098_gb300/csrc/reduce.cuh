@@ -100,9 +100,8 @@ __device__ __forceinline__ void finish_value(const Reduce &R, int v, double tota
                 S.active = 0;
                 S.paused = total > S.stop;
             }
-        } else {
-            S.beta = 0.0;
         }
+        // an inactive right-hand side keeps beta: a reliable update after a pause needs it
         break;
     case FIN_CDOT:
         if (v & 1) R.sc[v >> 1].last_im = total;
