@@ -207,7 +207,7 @@ def run_ours(args, world, rank, local):
         precise = precise_default if precise is None else precise
         rc, st = ctx.cg(MASS, bb, xb, tol=TOL, prec_sloppy=prec, prec_precise=precise, reliable_interval=100,
                         l2_persist=int(args.l2_persist),
-                        reliable_delta=0.1, profile=profile, host_buffers=host, stream=stream)
+                        reliable_delta=args.delta, profile=profile, host_buffers=host, stream=stream)
         if rc != hisq.OK:
             raise RuntimeError(f"solve did not converge: {st.as_dict()}")
         return st
@@ -296,7 +296,8 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_per_solve, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": f"{args.sloppy}+{args.precise}", "data": "synthetic",
         "config": {"workload": WORKLOAD, "lattice": "32x32x32x8", "sloppy": args.sloppy, "precise": args.precise,
-                   "reliable_interval": 100, "l2": "flushed between timed solves (256 MB write)",
+                   "reliable_interval": 100, "reliable_delta": args.delta,
+                   "l2": "flushed between timed solves (256 MB write)",
                    "l2_persist_links": {-1: "auto", 0: "off", 1: "on"}[args.l2_persist],
                    "parallelism": f"replicas x{world}"},
         "iterations": st.iterations, "reliable_updates": st.reliable_updates, "true_residual": st.true_residual,
@@ -325,6 +326,7 @@ def main():
     ap.add_argument("--sloppy", default="f16", choices=["f32", "f16", "bf16", "f64x"])
     ap.add_argument("--precise", default="f64", choices=["f64", "f64x"])
     ap.add_argument("--l2-persist", type=int, default=-1)
+    ap.add_argument("--delta", type=float, default=0.1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash-table", action="store_true")

@@ -161,8 +161,9 @@ typedef struct {
     int maxiter;           /* iteration cap (sloppy iterations)                              */
     int prec_sloppy;       /* precision of the iterated operator and vectors: HISQ_F64 gives
                               plain double CG; F64X/F32/F16/BF16 give mixed precision       */
-    int prec_precise;      /* operator for reliable updates and the final residual: HISQ_F64
-                              or HISQ_F64X                                                   */
+    int prec_precise;      /* operator of the reliable updates: HISQ_F64 or HISQ_F64X; with
+                              F64X the residual that ends the solve is recomputed with the
+                              FP64 operator (when built) before the solve is declared done */
     int reliable_interval; /* sloppy iterations between reliable updates (default 100)       */
     double reliable_delta; /* also update when |r| < delta * |r| at the last update (0.1)    */
     int zero_guess;        /* 1: start from x = 0; 0: x holds the initial guess              */

@@ -382,11 +382,11 @@ static int build_loop_graph(hisq_ctx *ctx, SolverWork &w, double m, const cudaAc
 }
 
 // r_hi = b - A_precise x_hi ; |r_hi|^2 -> Scalars.last
-int precise_residual(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st)
+int precise_residual(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, int prec)
 {
     int rc;
     const dim3 g(w.nblk_vec, w.nrhs);
-    if (w.pp == HISQ_F64) {
+    if (prec == HISQ_F64) {
         if ((rc = apply_mdagm(ctx, HISQ_F64, m, w.x64, w.thi, w.Axhi, w.nrhs, w.rb64, st, nullptr, true))) return rc;
         k_residual<HISQ_F64><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axhi, w.rb64}, VecRef{w.rhi, w.rb64},
                                                      w.Vh, w.red(FIN_STORE, w.nblk_vec));
@@ -440,7 +440,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
     if (o.zero_guess) {
         HISQ_CUDA(ctx, cudaMemcpyAsync(w.rhi, w.b64, vb, cudaMemcpyDeviceToDevice, st));
         k_norm_f64<<<g, kVecBlock, 0, st>>>(VecRef{w.rhi, w.rb64}, w.Vh, w.red(FIN_STORE, w.nblk_vec));
-    } else if ((rc = precise_residual(ctx, w, m, st))) {
+    } else if ((rc = precise_residual(ctx, w, m, st, w.pp))) {
         return rc;
     }
     k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_INIT_R, tol2, delta2);
@@ -533,7 +533,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         const bool last = it_all - it_start >= o.maxiter;
         if (any_flag || since_ru >= interval || !any_active || last) {
             dispatch(w.pv, [&](auto T) { decltype(T)::accum_hi(w, st); });
-            if ((rc = precise_residual(ctx, w, m, st))) return rc;
+            if ((rc = precise_residual(ctx, w, m, st, w.pp))) return rc;
             k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_RU, tol2, delta2);
             dispatch(w.pv, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
             kernels += 5 + (w.pp == HISQ_F64X ? 1 : 0);
@@ -542,6 +542,15 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             if ((rc = read_scalars(ctx, w, st))) return rc;
             bool any = false;
             for (int r = 0; r < nrhs; r++) any |= w.h_sc[r].active != 0;
+            if (!any && w.pp != HISQ_F64 && ctx->links[HISQ_F64].built) {
+                // converged by the float-pair operator: certify with the FP64 operator
+                if ((rc = precise_residual(ctx, w, m, st, HISQ_F64))) return rc;
+                k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_RU, tol2, delta2);
+                dispatch(w.pv, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
+                kernels += 5;
+                if ((rc = read_scalars(ctx, w, st))) return rc;
+                for (int r = 0; r < nrhs; r++) any |= w.h_sc[r].active != 0;
+            }
             if (!any || last) break;
             dispatch(w.pv, [&](auto T) { decltype(T)::reortho(w, st); });
             kernels += 2;
