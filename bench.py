@@ -326,7 +326,7 @@ def main():
     ap.add_argument("--sloppy", default="f16", choices=["f32", "f16", "bf16", "f64x"])
     ap.add_argument("--precise", default="f64", choices=["f64", "f64x"])
     ap.add_argument("--l2-persist", type=int, default=-1)
-    ap.add_argument("--delta", type=float, default=0.1)
+    ap.add_argument("--delta", type=float, default=0.01)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash-table", action="store_true")
