@@ -96,7 +96,8 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -206,7 +207,7 @@ def run_ours(args, world, rank, local):
     def solve(prec, precise=None, profile=0, xb=x, bb=b, host=0):
         precise = precise_default if precise is None else precise
         rc, st = ctx.cg(MASS, bb, xb, tol=TOL, prec_sloppy=prec, prec_precise=precise, reliable_interval=100,
-                        l2_persist=int(args.l2_persist),
+                        l2_persist=int(args.l2_persist), use_graph=int(args.use_graph),
                         reliable_delta=args.delta, profile=profile, host_buffers=host, stream=stream)
         if rc != hisq.OK:
             raise RuntimeError(f"solve did not converge: {st.as_dict()}")
@@ -299,6 +300,7 @@ def run_ours(args, world, rank, local):
                    "reliable_interval": 100, "reliable_delta": args.delta,
                    "l2": "flushed between timed solves (256 MB write)",
                    "l2_persist_links": {-1: "auto", 0: "off", 1: "on"}[args.l2_persist],
+                   "iteration_loop": "CUDA graph WHILE node" if args.use_graph else "direct launches",
                    "parallelism": f"replicas x{world}"},
         "iterations": st.iterations, "reliable_updates": st.reliable_updates, "true_residual": st.true_residual,
         "error_vs_fp64": err_vs_fp64, "fp64_cg_ms": fp64_ms, "fp64_iterations": st64.iterations,
@@ -327,6 +329,7 @@ def main():
     ap.add_argument("--precise", default="f64", choices=["f64", "f64x"])
     ap.add_argument("--l2-persist", type=int, default=-1)
     ap.add_argument("--delta", type=float, default=0.01)
+    ap.add_argument("--use-graph", type=int, default=1, help="0: direct launches (for ncu launch lists)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash-table", action="store_true")

@@ -1,0 +1,120 @@
+"""Solver throughput on the batched and large workloads (JSON lines).
+
+  python -m paper_2306_01098_gb300.solver_bench --workload batched   # 64^3 x 16
+  python -m paper_2306_01098_gb300.solver_bench --workload large     # 96^3 x 24, 12-real links
+
+batched: multi-RHS CG for nrhs in {1, 4, 8, 16} (16-bit links, FP32 vectors, FP64 reliable
+         updates), time per right-hand side against plain FP64 CG with one right-hand side, and
+         multi-shift CG with 14 shifts log-spaced 1e-5..1 (mixed and FP64).
+large:   multi-shift CG with 14 shifts on 96^3 x 24 with 12-real compressed 16-bit links and
+         FP64 reliable updates, plus the Dslash roofline of that link store.
+Every solve reports its residuals recomputed with the FP64 operator (tol 1e-10).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def _timed(fn, reps=1):
+    import torch
+    ts = []
+    out = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        ts.append(1e3 * (time.perf_counter() - t0))
+    return min(ts), out
+
+
+def batched(reps=2):
+    import torch
+
+    from hisq_inputs import fields, workloads
+    from paper_2306_01098_gb300 import hisq
+    w = workloads.BATCH_64x16
+    fat, lng = fields.recipe_links(w.dims, w.eps, w.link_seed, device="cuda")
+    ctx = hisq.Context(w.dims, fat, lng, precs=(hisq.F64, hisq.F32, hisq.F16))
+    del fat, lng
+    torch.cuda.empty_cache()
+    rows = []
+    b1 = fields.gaussian_source(w.dims, w.source_seed, 1, device="cuda")
+    x = torch.zeros_like(b1)
+    ms64, (rc, st) = _timed(lambda: ctx.cg(w.mass, b1, x.zero_(), tol=w.tol, prec_sloppy=hisq.F64), reps)
+    rows.append({"solve": "cg", "nrhs": 1, "sloppy": "f64", "ms": ms64, "ms_per_rhs": ms64, "iterations": st.iterations,
+                 "true_residual": st.true_residual, "rc": rc})
+    for nrhs in w.nrhs:
+        b = fields.gaussian_source(w.dims, w.source_seed, nrhs, device="cuda")
+        x = torch.zeros_like(b)
+        res = torch.zeros(nrhs, dtype=torch.float64)
+        ctx.cg(w.mass, b, x, tol=w.tol, prec_sloppy=hisq.F16, prec_precise=hisq.F64, reliable_delta=0.01)
+        ms, (rc, st) = _timed(lambda: ctx.cg(w.mass, b, x.zero_(), tol=w.tol, prec_sloppy=hisq.F16, prec_precise=hisq.F64,
+                                             reliable_delta=0.01, residuals=res), reps)
+        rows.append({"solve": "cg", "nrhs": nrhs, "sloppy": "f16", "ms": ms, "ms_per_rhs": ms / nrhs,
+                     "iterations": st.iterations, "reliable_updates": st.reliable_updates,
+                     "max_true_residual": float(res.max()), "speedup_per_rhs_vs_fp64": ms64 / (ms / nrhs), "rc": rc})
+    sig = list(w.shifts)
+    for prec, name in ((hisq.F64, "f64"), (hisq.F16, "f16")):
+        xs = [torch.zeros_like(b1[0]) for _ in sig]
+        res = torch.zeros(len(sig), dtype=torch.float64)
+        ms, (rc, st) = _timed(lambda: ctx.multishift_cg(w.mass, sig, b1[0].contiguous(), xs, tol=[w.tol] * len(sig),
+                                                        prec_sloppy=prec, prec_precise=hisq.F64, residuals=res), reps)
+        rows.append({"solve": "multishift", "nshift": len(sig), "sloppy": name, "ms": ms, "iterations": st.iterations,
+                     "max_true_residual": float(res.max()), "rc": rc})
+    ctx.close()
+    return rows
+
+
+def large(reps=1):
+    import torch
+
+    from hisq_inputs import fields, workloads
+    from paper_2306_01098_gb300 import dslash_bench, hisq
+    w = workloads.LARGE_96x24
+    t0 = time.perf_counter()
+    fat, lng = fields.recipe_links(w.dims, w.eps, w.link_seed, device="cuda")
+    gen_s = time.perf_counter() - t0
+    ctx = hisq.Context(w.dims, fat, lng, precs=(hisq.F64, hisq.F16), compression={hisq.F64: 18, hisq.F16: 12})
+    del fat, lng
+    torch.cuda.empty_cache()
+    rows = [{"step": "links", "generate_s": gen_s}]
+    b = fields.gaussian_source(w.dims, w.source_seed, 1, device="cuda")[0]
+    sig = list(w.shifts)
+    xs = [torch.zeros_like(b) for _ in sig]
+    res = torch.zeros(len(sig), dtype=torch.float64)
+    ms, (rc, st) = _timed(lambda: ctx.multishift_cg(w.mass, sig, b, xs, tol=[w.tol] * len(sig), prec_sloppy=hisq.F16,
+                                                    prec_precise=hisq.F64, reliable_delta=0.01, residuals=res), reps)
+    rows.append({"solve": "multishift", "lattice": "96x96x96x24", "links": "f16 12-real + f64 18-real",
+                 "nshift": len(sig), "ms": ms, "iterations": st.iterations, "reliable_updates": st.reliable_updates,
+                 "max_true_residual": float(res.max()), "rc": rc,
+                 "solves_per_s": 1e3 / ms, "site_shift_updates_per_s": ctx.Vh * len(sig) * st.iterations / (ms * 1e-3)})
+    ctx.close()
+    del xs, b
+    torch.cuda.empty_cache()
+    for r in dslash_bench.measure(w.dims, ("f16",), (1,), 12, reps=5, seed=w.link_seed):
+        r["workload"] = "96x96x96x24"
+        rows.append(r)
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", choices=["batched", "large"], default="batched")
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args()
+    rows = batched(a.reps) if a.workload == "batched" else large(a.reps)
+    for r in rows:
+        print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main()
