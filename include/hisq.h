@@ -214,6 +214,59 @@ int hisq_multishift_cg(hisq_ctx *ctx, double m, int nshift, const double *sigma,
                        const double *b, double *const *x, const double *tol,
                        const hisq_solve_opts *opts, hisq_stats *stats, double *residuals);
 
+/* ------------------------------------------------------------------ learned preconditioner */
+/* Not in the paper.  A gauge-covariant parallel-transport network K (layers of complex
+ * channel mixing over 17 taps: identity, the 8 one-hop and 8 three-hop transports of the
+ * Dslash stencil with the context's phased links) approximates A^-1 and preconditions
+ * flexible CG.  Weights: complex, layer l is a [17][C_out][C_in] block, layers concatenated;
+ * activations BF16, arithmetic FP32, gradients FP64. */
+typedef struct hisq_net hisq_net;
+
+typedef struct {
+    int nlayer;            /* layers (default 4); channels 1 -> C -> ... -> C -> 1           */
+    int channels;          /* hidden complex channels C: 1, 2, 4 or 8 (default 8)           */
+    int link_prec;         /* link store of the transports: HISQ_F32 (default) or HISQ_F16  */
+    int epochs;            /* passes over the training pairs (default 4)                    */
+    int batch;             /* pairs per Adam step (default 8)                               */
+    double lr, beta1, beta2, eps; /* Adam (default 2e-3, 0.9, 0.999, 1e-8)                  */
+    double init_hop;       /* scale of the random hopping weights at initialisation (0.05)  */
+    unsigned long long seed; /* initialisation and shuffling seed                           */
+} hisq_net_opts;
+
+void hisq_net_opts_default(hisq_net_opts *opts);
+/* Create a network on a context (the context must hold 18-real links of opts->link_prec).
+ * Weights start as the identity map plus small random hopping weights. */
+int hisq_net_create(hisq_ctx *ctx, const hisq_net_opts *opts, hisq_net **net);
+void hisq_net_destroy(hisq_net *net);
+/* number of complex weights, and host copies of them (interleaved re, im doubles) */
+long hisq_net_num_weights(const hisq_net *net);
+int hisq_net_get_weights(const hisq_net *net, double *w);
+int hisq_net_set_weights(hisq_net *net, const double *w);
+/* z = K(b): b, z canonical complex128 [Vh][3] even-site device buffers */
+int hisq_net_apply(hisq_net *net, const double *b, double *z, void *stream);
+/* loss |K(b) - x|^2 / |x|^2 and its gradient with respect to every weight (host array,
+ * interleaved complex, convention dL/dRe + i dL/dIm); b, x device [Vh][3] */
+int hisq_net_loss_grad(hisq_net *net, const double *b, const double *x, double *loss, double *grad);
+/* Train on npairs (b, x = A^-1 b) pairs, device arrays [npairs][Vh][3]: opts->epochs passes
+ * of shuffled mini-batches of opts->batch pairs, Adam.  The last layer's identity weight
+ * starts at <b,x>/<b,b> of the first pairs.  losses (may be NULL) receives the mean loss of
+ * every epoch. */
+int hisq_net_train(hisq_net *net, int npairs, const double *B, const double *X, double *losses);
+/* binary weights with a small header; load creates a network on ctx */
+int hisq_net_save(const hisq_net *net, const char *path);
+int hisq_net_load(hisq_ctx *ctx, const char *path, hisq_net **net);
+
+/* Flexible CG (inexact-preconditioner CG, Polak-Ribiere beta) on A x = b with z = K(r)
+ * (net != NULL) or z = r (net == NULL: reduces to CG):
+ *   alpha = <r,z>/<p,Ap>, x += alpha p, r' = r - alpha Ap, z' = K(r'),
+ *   beta = <r' - r, z'>/<r,z>, p = z' + beta p.
+ * FP64 vectors; A applied with opts->prec_precise (HISQ_F64 or HISQ_F64X); the final
+ * residual is recomputed with the FP64 operator.  b, x: canonical [Vh][3] device buffers.
+ * If the network output is not finite or the residual stops decreasing for 50 iterations,
+ * the solve continues as plain CG (stats->reliable_updates counts such fallbacks). */
+int hisq_fcg(hisq_ctx *ctx, double m, hisq_net *net, const double *b, double *x, const hisq_solve_opts *opts,
+             hisq_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,471 @@
+// net.cu -- gauge-covariant parallel-transport network (learned preconditioner; not in the
+// paper) with its forward, backward and Adam kernels, and the training loop.
+//
+// Layer l maps C_in -> C_out complex channels on the full lattice:
+//   psi'_{c'}(x) = sum_tap sum_c w[tap][c'][c] (T_tap psi_c)(x),
+//   tap 0 = identity; tap 1+2mu+s = one hop, tap 9+2mu+s = three hops (s = 0 forward,
+//   s = 1 backward) with the Dslash transports X_mu(x) psi(x+mu), X_mu(x-mu)^+ psi(x-mu),
+//   W_mu(x) psi(x+3mu), W_mu(x-3mu)^+ psi(x-3mu) of the phased links (the context's link store,
+//   where phases and the time boundary are folded in).  D itself is one such layer.
+// The network K maps a source on even sites (odd sites zero) through the layers and keeps
+// the even sites of the result.  Activations are stored in BF16 ([V][C][3 complex]),
+// arithmetic and weights in FP32; gradients are reduced in FP64.
+//   backward data:   g_in[c] = sum_tap sum_c' conj(w[tap][c'][c]) T_tap^+ g_out[c']
+//                    (T^+ of a forward tap is the backward tap of the same direction and
+//                    length, so the forward kernel runs with re-indexed conjugate weights)
+//   backward weights: G[tap][c'][c] = sum_x sum_colour conj((T_tap psi_c)(x)) g_out[c'](x)
+// Loss per (b, x) pair: |K(b) - x|^2 / |x|^2 on even sites.  Optimiser: Adam.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "arith.cuh"
+#include "blas.cuh"
+#include "net.cuh"
+
+namespace hisq {
+
+// ---------------------------------------------------------------- activation access
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ uint32_t bf_pack(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// channel c of site i: 3 complex numbers = 3 words
+template <int C>
+__device__ __forceinline__ void load_chan(const uint32_t *act, uint32_t i, int c, float (&v)[6])
+{
+    const uint32_t *p = act + ((size_t)i * C + c) * 3;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const uint32_t w = __ldg(p + k);
+        v[2 * k] = bf_lo(w);
+        v[2 * k + 1] = bf_hi(w);
+    }
+}
+
+struct NetLayerArgs {
+    Geom g;
+    const char *links;
+    size_t slot_bytes;
+    float scale[2];
+    const float2 *w;     // [17][cout][cin]
+    const uint32_t *in;  // [V][cin][3] bf16 complex
+    uint32_t *out;       // [V][cout][3]
+    int even_only_in;    // input lives on even sites only (odd sites read as zero)
+};
+
+template <int PL>
+__device__ __forceinline__ void tap_link(const NetLayerArgs &a, const Site &c, uint32_t s, int p, int mu, int h,
+                                         typename Prec<HISQ_F32>::Link &U, uint32_t &sn, bool &back, int &type)
+{
+    constexpr int LB = LinkBytes<PL>::b18;
+    const int k = h == 0 ? 1 : h == 1 ? -1 : h == 2 ? 3 : -3;
+    type = h >> 1;
+    back = h & 1;
+    bool wrap;
+    sn = neighbour(a.g, c, s, mu, k, wrap);
+    const int lp = back ? 1 - p : p;
+    const char *slot = a.links + (size_t)((lp * 2 + type) * 4 + mu) * a.slot_bytes;
+    uint32_t w[LB / 4];
+    load_link_words<LB>(slot, back ? sn : s, w);
+    Prec<PL>::template unpack<18>(w, U);
+    if constexpr (PL == HISQ_F16 || PL == HISQ_BF16) {
+        const float sc = a.scale[type];
+#pragma unroll
+        for (int q = 0; q < 18; q++) U.v[q] *= sc;
+    }
+}
+
+__device__ __forceinline__ void transport(const typename Prec<HISQ_F32>::Link &U, bool dag, const float (&v)[6],
+                                          float (&t)[6])
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float ur = dag ? U.v[2 * (3 * j + i)] : U.v[2 * (3 * i + j)];
+            const float ui = dag ? -U.v[2 * (3 * j + i) + 1] : U.v[2 * (3 * i + j) + 1];
+            re = fmaf(ur, v[2 * j], fmaf(-ui, v[2 * j + 1], re));
+            im = fmaf(ur, v[2 * j + 1], fmaf(ui, v[2 * j], im));
+        }
+        t[2 * i] = re;
+        t[2 * i + 1] = im;
+    }
+}
+
+// forward layer (also the backward-data pass with re-indexed conjugate weights)
+template <int PL, int CIN, int COUT>
+__global__ void __launch_bounds__(128) k_net_layer(const NetLayerArgs a)
+{
+    __shared__ float2 sw[kNetTaps * COUT * CIN];
+    for (int q = threadIdx.x; q < kNetTaps * COUT * CIN; q += blockDim.x) sw[q] = a.w[q];
+    __syncthreads();
+    const uint32_t V = 2 * a.g.Vh;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V) return;
+    const int p = i >= a.g.Vh;
+    const uint32_t s = i - p * a.g.Vh;
+    float acc[COUT][6];
+#pragma unroll
+    for (int o = 0; o < COUT; o++)
+#pragma unroll
+        for (int k = 0; k < 6; k++) acc[o][k] = 0.f;
+    // tap 0: identity
+    if (!(a.even_only_in && p)) {
+#pragma unroll
+        for (int ci = 0; ci < CIN; ci++) {
+            float v[6];
+            load_chan<CIN>(a.in, i, ci, v);
+#pragma unroll
+            for (int o = 0; o < COUT; o++) {
+                const float2 w = sw[o * CIN + ci];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    acc[o][2 * k] = fmaf(w.x, v[2 * k], fmaf(-w.y, v[2 * k + 1], acc[o][2 * k]));
+                    acc[o][2 * k + 1] = fmaf(w.x, v[2 * k + 1], fmaf(w.y, v[2 * k], acc[o][2 * k + 1]));
+                }
+            }
+        }
+    }
+    const Site c = site_coords(a.g, s, p);
+    const bool nb_zero = a.even_only_in && (1 - p); // neighbours are odd: zero input
+    if (!nb_zero) {
+#pragma unroll 1
+        for (int mu = 0; mu < 4; mu++) {
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                typename Prec<HISQ_F32>::Link U;
+                uint32_t sn;
+                bool back;
+                int type;
+                tap_link<PL>(a, c, s, p, mu, h, U, sn, back, type);
+                const int tap = (type ? 9 : 1) + 2 * mu + (back ? 1 : 0);
+                const uint32_t n = sn + (uint32_t)(1 - p) * a.g.Vh;
+#pragma unroll
+                for (int ci = 0; ci < CIN; ci++) {
+                    float v[6], t[6];
+                    load_chan<CIN>(a.in, n, ci, v);
+                    transport(U, back, v, t);
+#pragma unroll
+                    for (int o = 0; o < COUT; o++) {
+                        const float2 w = sw[(tap * COUT + o) * CIN + ci];
+#pragma unroll
+                        for (int k = 0; k < 3; k++) {
+                            acc[o][2 * k] = fmaf(w.x, t[2 * k], fmaf(-w.y, t[2 * k + 1], acc[o][2 * k]));
+                            acc[o][2 * k + 1] = fmaf(w.x, t[2 * k + 1], fmaf(w.y, t[2 * k], acc[o][2 * k + 1]));
+                        }
+                    }
+                }
+            }
+        }
+    }
+    uint32_t *q = a.out + (size_t)i * COUT * 3;
+#pragma unroll
+    for (int o = 0; o < COUT; o++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) q[o * 3 + k] = bf_pack(acc[o][2 * k], acc[o][2 * k + 1]);
+}
+
+// weight gradient: per block partial sums of G[tap][c'][c] (complex) -> part[block][17*cout*cin]
+template <int PL, int CIN, int COUT>
+__global__ void __launch_bounds__(128) k_net_wgrad(const NetLayerArgs a, const uint32_t *gout, float2 *part)
+{
+    __shared__ float2 sg[kNetTaps * COUT * CIN];
+    for (int q = threadIdx.x; q < kNetTaps * COUT * CIN; q += blockDim.x) sg[q] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const uint32_t V = 2 * a.g.Vh;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < V;
+    const int p = live ? (i >= a.g.Vh) : 0;
+    const uint32_t s = live ? i - p * a.g.Vh : 0;
+    const int lane = threadIdx.x & 31;
+    float g[COUT][6];
+#pragma unroll
+    for (int o = 0; o < COUT; o++) {
+        if (live) load_chan<COUT>(gout, i, o, g[o]);
+        else
+#pragma unroll
+            for (int k = 0; k < 6; k++) g[o][k] = 0.f;
+    }
+    const Site c = site_coords(a.g, s, p);
+    for (int tap = 0; tap < kNetTaps; tap++) {
+        typename Prec<HISQ_F32>::Link U;
+        uint32_t n = i;
+        bool back = false, zero = !live;
+        if (tap > 0) {
+            const int k = tap - 1, three = k >= 8, mu = (k & 7) >> 1, bk = k & 1;
+            const int h = three * 2 + bk;
+            uint32_t sn = 0;
+            int type;
+            if (live) {
+                tap_link<PL>(a, c, s, p, mu, h, U, sn, back, type);
+                n = sn + (uint32_t)(1 - p) * a.g.Vh;
+            }
+            if (a.even_only_in && p == 0) zero = true; // neighbours of even sites are odd
+        } else if (a.even_only_in && p == 1) {
+            zero = true;
+        }
+        for (int ci = 0; ci < CIN; ci++) {
+            float t[6];
+            if (!zero) {
+                float v[6];
+                load_chan<CIN>(a.in, n, ci, v);
+                if (tap > 0) transport(U, back, v, t);
+                else
+#pragma unroll
+                    for (int k = 0; k < 6; k++) t[k] = v[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 6; k++) t[k] = 0.f;
+            }
+#pragma unroll
+            for (int o = 0; o < COUT; o++) {
+                // conj(t) . g
+                float re = 0.f, im = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    re = fmaf(t[2 * k], g[o][2 * k], fmaf(t[2 * k + 1], g[o][2 * k + 1], re));
+                    im = fmaf(t[2 * k], g[o][2 * k + 1], fmaf(-t[2 * k + 1], g[o][2 * k], im));
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    re += __shfl_xor_sync(0xffffffffu, re, off);
+                    im += __shfl_xor_sync(0xffffffffu, im, off);
+                }
+                if (lane == 0) {
+                    atomicAdd(&sg[(tap * COUT + o) * CIN + ci].x, re);
+                    atomicAdd(&sg[(tap * COUT + o) * CIN + ci].y, im);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kNetTaps * COUT * CIN; q += blockDim.x)
+        part[(size_t)blockIdx.x * kNetTaps * COUT * CIN + q] = sg[q];
+}
+
+// sum the block partials in a fixed order (FP64) and add to grad
+__global__ void k_net_wgrad_reduce(const float2 *part, int nblocks, int nw, double2 *grad)
+{
+    const int q = blockIdx.x;
+    double re = 0.0, im = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const float2 v = part[(size_t)b * nw + q];
+        re += v.x;
+        im += v.y;
+    }
+    re = block_sum(re);
+    __syncthreads();
+    im = block_sum(im);
+    if (threadIdx.x == 0) {
+        grad[q].x += re;
+        grad[q].y += im;
+    }
+}
+
+// w'[tap'][c][c'] = conj(w[adj(tap')][c'][c]) for the backward-data pass
+__global__ void k_net_adjoint_weights(const float2 *w, float2 *wa, int cin, int cout)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= kNetTaps * cin * cout) return;
+    const int tp = q / (cin * cout), rem = q % (cin * cout);
+    const int ci = rem / cout, co = rem % cout; // wa layout [tap'][cin (now out)][cout (now in)]
+    const int tap = tp == 0 ? 0 : (((tp - 1) ^ 1) + 1);
+    const float2 v = w[(tap * cout + co) * cin + ci];
+    wa[(tp * cin + ci) * cout + co] = make_float2(v.x, -v.y);
+}
+
+// b (canonical F64, even sites) -> 1-channel BF16 activation on the full lattice
+__global__ void k_net_input(const double *b, uint32_t *act, uint32_t Vh)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * Vh) return;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        act[(size_t)i * 3 + k] = i < Vh ? bf_pack((float)b[(size_t)i * 6 + 2 * k], (float)b[(size_t)i * 6 + 2 * k + 1]) : 0u;
+}
+
+// z (canonical F64, even sites) from the 1-channel output activation
+__global__ void k_net_output(const uint32_t *act, double *z, uint32_t Vh)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Vh) return;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const uint32_t w = act[(size_t)i * 3 + k];
+        z[(size_t)i * 6 + 2 * k] = bf_lo(w);
+        z[(size_t)i * 6 + 2 * k + 1] = bf_hi(w);
+    }
+}
+
+// loss pieces: d = z - x on even sites; partial |d|^2 and |x|^2 (FIN_STORE values 0, 1)
+__global__ void k_net_loss(const uint32_t *zact, const double *x, uint32_t Vh, Reduce red)
+{
+    double dd = 0.0, xx = 0.0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const uint32_t w = zact[(size_t)i * 3 + k];
+            const double xr = x[(size_t)i * 6 + 2 * k], xi = x[(size_t)i * 6 + 2 * k + 1];
+            const double dr = bf_lo(w) - xr, di = bf_hi(w) - xi;
+            dd += dr * dr + di * di;
+            xx += xr * xr + xi * xi;
+        }
+    }
+    double mine[2] = {block_sum(dd), 0.0};
+    __syncthreads();
+    mine[1] = block_sum(xx);
+    grid_reduce<2>(red, mine, 2, 0, 2, blockIdx.x);
+}
+
+// g = 2 (z - x) / |x|^2 on even sites, 0 on odd sites (1-channel BF16)
+__global__ void k_net_loss_grad(const uint32_t *zact, const double *x, uint32_t *g, uint32_t Vh, const Scalars *sc,
+                                double weight)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * Vh) return;
+    const double f = weight * 2.0 / sc[1].last;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        uint32_t out = 0u;
+        if (i < Vh) {
+            const uint32_t w = zact[(size_t)i * 3 + k];
+            out = bf_pack((float)(f * (bf_lo(w) - x[(size_t)i * 6 + 2 * k])),
+                          (float)(f * (bf_hi(w) - x[(size_t)i * 6 + 2 * k + 1])));
+        }
+        g[(size_t)i * 3 + k] = out;
+    }
+}
+
+// ---------------------------------------------------------------- launch helpers
+template <int PL>
+static cudaError_t launch_layer_pl(const NetLayerArgs &a, int cin, int cout, cudaStream_t st)
+{
+    const unsigned V = 2 * a.g.Vh, nb = (V + 127) / 128;
+#define HISQ_NET_CASE(CI, CO)                                                     \
+    if (cin == CI && cout == CO) {                                                \
+        k_net_layer<PL, CI, CO><<<nb, 128, 0, st>>>(a);                           \
+        return cudaGetLastError();                                                \
+    }
+    HISQ_NET_CASE(1, kNetMaxChan) HISQ_NET_CASE(kNetMaxChan, kNetMaxChan) HISQ_NET_CASE(kNetMaxChan, 1)
+    HISQ_NET_CASE(1, 1) HISQ_NET_CASE(1, 2) HISQ_NET_CASE(2, 2) HISQ_NET_CASE(2, 1) HISQ_NET_CASE(1, 4)
+    HISQ_NET_CASE(4, 4) HISQ_NET_CASE(4, 1)
+#undef HISQ_NET_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <int PL>
+static cudaError_t launch_wgrad_pl(const NetLayerArgs &a, const uint32_t *g, float2 *part, int cin, int cout,
+                                   cudaStream_t st)
+{
+    const unsigned V = 2 * a.g.Vh, nb = (V + 127) / 128;
+#define HISQ_NET_CASE(CI, CO)                                                     \
+    if (cin == CI && cout == CO) {                                                \
+        k_net_wgrad<PL, CI, CO><<<nb, 128, 0, st>>>(a, g, part);                  \
+        return cudaGetLastError();                                                \
+    }
+    HISQ_NET_CASE(1, kNetMaxChan) HISQ_NET_CASE(kNetMaxChan, kNetMaxChan) HISQ_NET_CASE(kNetMaxChan, 1)
+    HISQ_NET_CASE(1, 1) HISQ_NET_CASE(1, 2) HISQ_NET_CASE(2, 2) HISQ_NET_CASE(2, 1) HISQ_NET_CASE(1, 4)
+    HISQ_NET_CASE(4, 4) HISQ_NET_CASE(4, 1)
+#undef HISQ_NET_CASE
+    return cudaErrorInvalidValue;
+}
+
+bool net_shape_supported(int cin, int cout)
+{
+    const int ok[][2] = {{1, kNetMaxChan}, {kNetMaxChan, kNetMaxChan}, {kNetMaxChan, 1}, {1, 1}, {1, 2},
+                         {2, 2}, {2, 1}, {1, 4}, {4, 4}, {4, 1}};
+    for (auto &q : ok)
+        if (q[0] == cin && q[1] == cout) return true;
+    return false;
+}
+
+static NetLayerArgs layer_args(const hisq_net *n, const float2 *w, const uint32_t *in, uint32_t *out, int even_in)
+{
+    NetLayerArgs a{};
+    const LinkStore &L = n->ctx->links[n->link_prec];
+    a.g = n->ctx->g;
+    a.links = L.base;
+    a.slot_bytes = L.slot_bytes;
+    a.scale[0] = (float)L.scale[0];
+    a.scale[1] = (float)L.scale[1];
+    a.w = w;
+    a.in = in;
+    a.out = out;
+    a.even_only_in = even_in;
+    return a;
+}
+
+cudaError_t net_layer(const hisq_net *n, const float2 *w, const uint32_t *in, uint32_t *out, int cin, int cout,
+                      int even_in, cudaStream_t st)
+{
+    const NetLayerArgs a = layer_args(n, w, in, out, even_in);
+    return n->link_prec == HISQ_F16 ? launch_layer_pl<HISQ_F16>(a, cin, cout, st)
+                                    : launch_layer_pl<HISQ_F32>(a, cin, cout, st);
+}
+
+cudaError_t net_wgrad(const hisq_net *n, const uint32_t *in, const uint32_t *g, float2 *part, int cin, int cout,
+                      int even_in, cudaStream_t st)
+{
+    const NetLayerArgs a = layer_args(n, nullptr, in, nullptr, even_in);
+    return n->link_prec == HISQ_F16 ? launch_wgrad_pl<HISQ_F16>(a, g, part, cin, cout, st)
+                                    : launch_wgrad_pl<HISQ_F32>(a, g, part, cin, cout, st);
+}
+
+// z = K(b): b, z canonical complex128 [Vh][3] device buffers
+int net_forward(hisq_net *n, const double *b, double *z, cudaStream_t st)
+{
+    const uint32_t Vh = n->ctx->g.Vh, V = 2 * Vh;
+    k_net_input<<<(V + 255) / 256, 256, 0, st>>>(b, n->act[0], Vh);
+    for (int l = 0; l < n->nlayer; l++) {
+        cudaError_t e = net_layer(n, n->w + n->woff[l], n->act[l], n->act[l + 1], n->chans[l], n->chans[l + 1],
+                                  l == 0, st);
+        if (e != cudaSuccess) return cuda_error(n->ctx, e, "network layer");
+    }
+    if (z) k_net_output<<<(Vh + 255) / 256, 256, 0, st>>>(n->act[n->nlayer], z, Vh);
+    HISQ_CUDA(n->ctx, cudaGetLastError());
+    return HISQ_OK;
+}
+
+// one (b, x) pair: forward, loss, gradient accumulated into n->grad (weight `scale`)
+int net_accumulate(hisq_net *n, const double *b, const double *x, double scale, cudaStream_t st)
+{
+    const uint32_t Vh = n->ctx->g.Vh, V = 2 * Vh;
+    int rc = net_forward(n, b, nullptr, st);
+    if (rc) return rc;
+    Reduce R;
+    R.partials = n->partials;
+    R.counter = n->counter;
+    R.sc = n->sc;
+    R.op = FIN_STORE;
+    R.nblocks = n->nblk_vec;
+    R.ntotal = n->nblk_vec;
+    k_net_loss<<<n->nblk_vec, kVecBlock, 0, st>>>(n->act[n->nlayer], x, Vh, R);
+    k_net_loss_grad<<<(V + 255) / 256, 256, 0, st>>>(n->act[n->nlayer], x, n->gact[0], Vh, n->sc, scale);
+    HISQ_CUDA(n->ctx, cudaGetLastError());
+    uint32_t *g = n->gact[0], *gnext = n->gact[1];
+    for (int l = n->nlayer - 1; l >= 0; l--) {
+        const int cin = n->chans[l], cout = n->chans[l + 1];
+        const int nblocks = (int)((V + 127) / 128);
+        cudaError_t e = net_wgrad(n, n->act[l], g, n->part, cin, cout, l == 0, st);
+        if (e != cudaSuccess) return cuda_error(n->ctx, e, "network weight gradient");
+        const int nw = kNetTaps * cin * cout;
+        k_net_wgrad_reduce<<<nw, 256, 0, st>>>(n->part, nblocks, nw, n->grad + n->woff[l]);
+        if (l > 0) {
+            k_net_adjoint_weights<<<(nw + 127) / 128, 128, 0, st>>>(n->w + n->woff[l], n->wadj, cin, cout);
+            e = net_layer(n, n->wadj, g, gnext, cout, cin, 0, st);
+            if (e != cudaSuccess) return cuda_error(n->ctx, e, "network backward layer");
+            std::swap(g, gnext);
+        }
+    }
+    HISQ_CUDA(n->ctx, cudaGetLastError());
+    return HISQ_OK;
+}
+
+}  // namespace hisq

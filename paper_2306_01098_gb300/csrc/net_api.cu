@@ -1,0 +1,540 @@
+// net_api.cu -- C entry points of the learned preconditioner: network creation, weights,
+// inference, loss gradient, training (Adam), persistence, and flexible CG with K = network.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <random>
+#include <vector>
+
+#include "blas.cuh"
+#include "dslash.cuh"
+#include "net.cuh"
+
+namespace hisq {
+
+int apply_mdagm(hisq_ctx *ctx, int prec, double m, const void *in, void *tmp, void *out, int nrhs, size_t rhs_bytes,
+                cudaStream_t st, const Reduce *red, bool tune);
+
+static int net_alloc(hisq_net *n, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return cuda_error(n->ctx, e, "network allocation");
+    cudaMemset(*p, 0, bytes ? bytes : 16);
+    n->allocs.push_back(*p);
+    return HISQ_OK;
+}
+
+static void net_free(hisq_net *n)
+{
+    if (!n) return;
+    for (void *p : n->allocs) cudaFree(p);
+    n->allocs.clear();
+    if (n->h_sc) cudaFreeHost(n->h_sc);
+    if (n->st) cudaStreamDestroy(n->st);
+    delete n;
+}
+
+static Reduce net_red(const hisq_net *n, int op, int nblocks, int ntotal)
+{
+    Reduce R;
+    R.partials = n->partials;
+    R.counter = n->counter;
+    R.sc = n->sc;
+    R.op = op;
+    R.nblocks = nblocks;
+    R.ntotal = ntotal;
+    return R;
+}
+
+static int read_sc(hisq_net *n, cudaStream_t st)
+{
+    HISQ_CUDA(n->ctx, cudaMemcpyAsync(n->h_sc, n->sc, sizeof(Scalars) * 4, cudaMemcpyDeviceToHost, st));
+    HISQ_CUDA(n->ctx, cudaStreamSynchronize(st));
+    return HISQ_OK;
+}
+
+// initial weights: identity map, plus small seeded random hopping weights
+static void init_weights(const hisq_net *n, std::vector<float> &w)
+{
+    std::mt19937_64 rng(n->opts.seed);
+    std::normal_distribution<double> N(0.0, 1.0);
+    w.assign(2 * (size_t)n->nw, 0.f);
+    for (int l = 0; l < n->nlayer; l++) {
+        const int cin = n->chans[l], cout = n->chans[l + 1];
+        const double sd = n->opts.init_hop / std::sqrt((double)kNetTaps * cin);
+        for (int tap = 0; tap < kNetTaps; tap++)
+            for (int o = 0; o < cout; o++)
+                for (int i = 0; i < cin; i++) {
+                    const size_t q = 2 * ((size_t)n->woff[l] + ((size_t)tap * cout + o) * cin + i);
+                    const double re = N(rng), im = N(rng);
+                    if (tap == 0) {
+                        w[q] = (o == i) ? 1.f : 0.f;
+                    } else {
+                        w[q] = (float)(sd * re);
+                        w[q + 1] = (float)(sd * im);
+                    }
+                }
+    }
+}
+
+// Adam on the real and imaginary parts of every weight (Kingma & Ba 2015)
+__global__ void k_adam(float2 *w, const double2 *grad, float2 *m1, float2 *m2, int n, float lr, float b1, float b2,
+                       float eps, int step)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    const float g[2] = {(float)grad[q].x, (float)grad[q].y};
+    float *pw = reinterpret_cast<float *>(&w[q]);
+    float *pm = reinterpret_cast<float *>(&m1[q]);
+    float *pv = reinterpret_cast<float *>(&m2[q]);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        pm[k] = b1 * pm[k] + (1.f - b1) * g[k];
+        pv[k] = b2 * pv[k] + (1.f - b2) * g[k] * g[k];
+        pw[k] -= lr * (pm[k] / c1) / (sqrtf(pv[k] / c2) + eps);
+    }
+}
+
+__global__ void k_loss_accum(const Scalars *sc, double *acc)
+{
+    *acc += sc[0].last / sc[1].last;
+}
+
+// FCG vector updates with complex coefficients, FP64 canonical vectors
+__global__ void k_fcg_update(double2 *x, const double2 *p, const double2 *q, const double2 *r, double2 *rn, size_t n,
+                             double ar, double ai)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 pv = p[i], qv = q[i], rv = r[i];
+        double2 xv = x[i];
+        xv.x += ar * pv.x - ai * pv.y;
+        xv.y += ar * pv.y + ai * pv.x;
+        x[i] = xv;
+        rn[i] = make_double2(rv.x - (ar * qv.x - ai * qv.y), rv.y - (ar * qv.y + ai * qv.x));
+    }
+}
+
+__global__ void k_fcg_p(double2 *p, const double2 *z, size_t n, double br, double bi)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 pv = p[i], zv = z[i];
+        p[i] = make_double2(zv.x + br * pv.x - bi * pv.y, zv.y + br * pv.y + bi * pv.x);
+    }
+}
+
+__global__ void k_sub(const double2 *a, const double2 *b, double2 *c, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        c[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
+}
+
+__global__ void k_finite(const double *v, size_t n, int *bad)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) *bad = 1;
+}
+
+}  // namespace hisq
+
+using namespace hisq;
+
+extern "C" {
+
+void hisq_net_opts_default(hisq_net_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->nlayer = 4;
+    o->channels = 8;
+    o->link_prec = HISQ_F32;
+    o->epochs = 4;
+    o->batch = 8;
+    o->lr = 2e-3;
+    o->beta1 = 0.9;
+    o->beta2 = 0.999;
+    o->eps = 1e-8;
+    o->init_hop = 0.05;
+    o->seed = 12345;
+}
+
+int hisq_net_create(hisq_ctx *ctx, const hisq_net_opts *opts_in, hisq_net **out)
+{
+    if (!ctx || !out) return HISQ_EINVAL;
+    *out = nullptr;
+    hisq_net_opts o;
+    if (opts_in) o = *opts_in;
+    else hisq_net_opts_default(&o);
+    if (o.nlayer < 1 || o.nlayer > kNetMaxLayers || o.batch < 1 || o.epochs < 0 || !(o.lr > 0.0))
+        return set_error(ctx, HISQ_EINVAL, "hisq_net_create: bad options");
+    if (o.link_prec != HISQ_F32 && o.link_prec != HISQ_F16) return set_error(ctx, HISQ_EINVAL, "hisq_net_create: link precision");
+    if (!ctx->links[o.link_prec].built || ctx->links[o.link_prec].nreal != 18)
+        return set_error(ctx, HISQ_ENOTBUILT, "hisq_net_create: needs 18-real links of that precision");
+    hisq_net *n = new hisq_net();
+    n->ctx = ctx;
+    n->opts = o;
+    n->nlayer = o.nlayer;
+    n->link_prec = o.link_prec;
+    n->chans[0] = n->chans[o.nlayer] = 1;
+    for (int l = 1; l < o.nlayer; l++) n->chans[l] = o.channels;
+    int nw = 0, maxc = 1;
+    for (int l = 0; l < o.nlayer; l++) {
+        if (!net_shape_supported(n->chans[l], n->chans[l + 1])) {
+            delete n;
+            return set_error(ctx, HISQ_EINVAL, "hisq_net_create: channel count must be 1, 2, 4 or 8");
+        }
+        n->woff[l] = nw;
+        nw += kNetTaps * n->chans[l] * n->chans[l + 1];
+        maxc = std::max(maxc, n->chans[l + 1]);
+    }
+    n->woff[o.nlayer] = nw;
+    n->nw = nw;
+    const size_t V = 2ull * ctx->g.Vh;
+    const int nblocks = (int)((V + 127) / 128);
+    n->nblk_vec = (int)std::min<size_t>((ctx->g.Vh + kVecBlock - 1) / kVecBlock, 4ull * ctx->sm_count);
+    int rc = HISQ_OK;
+    auto A = [&](void **p, size_t b) { if (rc == HISQ_OK) rc = net_alloc(n, p, b); };
+    A((void **)&n->w, sizeof(float2) * nw);
+    A((void **)&n->wadj, sizeof(float2) * kNetTaps * kNetMaxChan * kNetMaxChan);
+    A((void **)&n->m1, sizeof(float2) * nw);
+    A((void **)&n->m2, sizeof(float2) * nw);
+    A((void **)&n->grad, sizeof(double2) * nw);
+    for (int l = 0; l <= o.nlayer; l++) A((void **)&n->act[l], V * n->chans[l] * 12);
+    A((void **)&n->gact[0], V * maxc * 12);
+    A((void **)&n->gact[1], V * maxc * 12);
+    A((void **)&n->part, sizeof(float2) * (size_t)nblocks * kNetTaps * kNetMaxChan * kNetMaxChan);
+    A((void **)&n->partials, sizeof(double) * 8 * (size_t)std::max(n->nblk_vec, nblocks));
+    A((void **)&n->counter, 64);
+    A((void **)&n->sc, sizeof(Scalars) * 4);
+    A((void **)&n->lossacc, sizeof(double));
+    if (rc) {
+        net_free(n);
+        return rc;
+    }
+    if (cudaMallocHost(&n->h_sc, sizeof(Scalars) * 4) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&n->st, cudaStreamNonBlocking) != cudaSuccess) {
+        net_free(n);
+        return set_error(ctx, HISQ_ENOMEM, "hisq_net_create: host resources");
+    }
+    std::vector<float> w;
+    init_weights(n, w);
+    cudaError_t e = cudaMemcpy(n->w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        net_free(n);
+        return cuda_error(ctx, e, "hisq_net_create: weights");
+    }
+    *out = n;
+    return HISQ_OK;
+}
+
+void hisq_net_destroy(hisq_net *n)
+{
+    if (!n) return;
+    cudaSetDevice(n->ctx->device);
+    cudaDeviceSynchronize();
+    net_free(n);
+}
+
+long hisq_net_num_weights(const hisq_net *n) { return n ? n->nw : 0; }
+
+int hisq_net_get_weights(const hisq_net *n, double *w)
+{
+    if (!n || !w) return HISQ_EINVAL;
+    std::vector<float2> h(n->nw);
+    HISQ_CUDA(n->ctx, cudaMemcpy(h.data(), n->w, sizeof(float2) * n->nw, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n->nw; i++) {
+        w[2 * i] = h[i].x;
+        w[2 * i + 1] = h[i].y;
+    }
+    return HISQ_OK;
+}
+
+int hisq_net_set_weights(hisq_net *n, const double *w)
+{
+    if (!n || !w) return HISQ_EINVAL;
+    std::vector<float2> h(n->nw);
+    for (int i = 0; i < n->nw; i++) h[i] = make_float2((float)w[2 * i], (float)w[2 * i + 1]);
+    HISQ_CUDA(n->ctx, cudaMemcpy(n->w, h.data(), sizeof(float2) * n->nw, cudaMemcpyHostToDevice));
+    return HISQ_OK;
+}
+
+int hisq_net_apply(hisq_net *n, const double *b, double *z, void *stream)
+{
+    if (!n || !b || !z) return HISQ_EINVAL;
+    return net_forward(n, b, z, (cudaStream_t)stream);
+}
+
+int hisq_net_loss_grad(hisq_net *n, const double *b, const double *x, double *loss, double *grad)
+{
+    if (!n || !b || !x) return HISQ_EINVAL;
+    cudaStream_t st = n->st;
+    HISQ_CUDA(n->ctx, cudaMemsetAsync(n->grad, 0, sizeof(double2) * n->nw, st));
+    int rc = net_accumulate(n, b, x, 1.0, st);
+    if (rc) return rc;
+    if ((rc = read_sc(n, st))) return rc;
+    if (loss) *loss = n->h_sc[0].last / n->h_sc[1].last;
+    if (grad) HISQ_CUDA(n->ctx, cudaMemcpy(grad, n->grad, sizeof(double2) * n->nw, cudaMemcpyDeviceToHost));
+    return HISQ_OK;
+}
+
+int hisq_net_train(hisq_net *n, int npairs, const double *B, const double *X, double *losses)
+{
+    if (!n || npairs < 1 || !B || !X) return HISQ_EINVAL;
+    hisq_ctx *ctx = n->ctx;
+    cudaStream_t st = n->st;
+    const uint32_t Vh = ctx->g.Vh;
+    const size_t vec = (size_t)Vh * 6; // doubles per vector
+    // the scale of A^-1 seen by the data: <b,x>/<b,b> averaged over the first pairs
+    double ratio = 0.0;
+    const int nprobe = std::min(npairs, 8);
+    for (int i = 0; i < nprobe; i++) {
+        const double *b = B + i * vec, *x = X + i * vec;
+        const dim3 g(n->nblk_vec, 1);
+        k_cdot<HISQ_F64><<<g, kVecBlock, 0, st>>>(VecRef{(char *)b, 0}, VecRef{(char *)x, 0}, Vh,
+                                                  net_red(n, FIN_CDOT, n->nblk_vec, n->nblk_vec));
+        int rc = read_sc(n, st);
+        if (rc) return rc;
+        const double bx = n->h_sc[0].last;
+        k_norm_f64<<<g, kVecBlock, 0, st>>>(VecRef{(char *)b, 0}, Vh, net_red(n, FIN_STORE, n->nblk_vec, n->nblk_vec));
+        if ((rc = read_sc(n, st))) return rc;
+        ratio += bx / n->h_sc[0].last;
+    }
+    ratio /= nprobe;
+    const int last = n->nlayer - 1;
+    const float2 s0 = make_float2((float)ratio, 0.f);
+    HISQ_CUDA(ctx, cudaMemcpyAsync(n->w + n->woff[last], &s0, sizeof(float2), cudaMemcpyHostToDevice, st));
+    std::vector<int> order(npairs);
+    std::iota(order.begin(), order.end(), 0);
+    std::mt19937_64 rng(n->opts.seed ^ 0x5bd1e995ull);
+    const int bs = n->opts.batch;
+    for (int ep = 0; ep < n->opts.epochs; ep++) {
+        std::shuffle(order.begin(), order.end(), rng);
+        HISQ_CUDA(ctx, cudaMemsetAsync(n->lossacc, 0, sizeof(double), st));
+        for (int b0 = 0; b0 < npairs; b0 += bs) {
+            const int nb = std::min(bs, npairs - b0);
+            HISQ_CUDA(ctx, cudaMemsetAsync(n->grad, 0, sizeof(double2) * n->nw, st));
+            for (int k = 0; k < nb; k++) {
+                const int i = order[b0 + k];
+                int rc = net_accumulate(n, B + i * vec, X + i * vec, 1.0 / nb, st);
+                if (rc) return rc;
+                k_loss_accum<<<1, 1, 0, st>>>(n->sc, n->lossacc);
+            }
+            n->step++;
+            k_adam<<<(n->nw + 127) / 128, 128, 0, st>>>(n->w, n->grad, n->m1, n->m2, n->nw, (float)n->opts.lr,
+                                                         (float)n->opts.beta1, (float)n->opts.beta2, (float)n->opts.eps,
+                                                         n->step);
+            HISQ_CUDA(ctx, cudaGetLastError());
+        }
+        double acc = 0.0;
+        HISQ_CUDA(ctx, cudaMemcpyAsync(&acc, n->lossacc, sizeof(double), cudaMemcpyDeviceToHost, st));
+        HISQ_CUDA(ctx, cudaStreamSynchronize(st));
+        if (losses) losses[ep] = acc / npairs;
+    }
+    HISQ_CUDA(ctx, cudaStreamSynchronize(st));
+    return HISQ_OK;
+}
+
+int hisq_net_save(const hisq_net *n, const char *path)
+{
+    if (!n || !path) return HISQ_EINVAL;
+    std::vector<double> w(2 * (size_t)n->nw);
+    int rc = hisq_net_get_weights(n, w.data());
+    if (rc) return rc;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return set_error(n->ctx, HISQ_EINVAL, "hisq_net_save: cannot open file");
+    const char magic[8] = {'H', 'I', 'S', 'Q', 'N', 'E', 'T', '1'};
+    const int hdr[4] = {n->nlayer, n->opts.channels, n->link_prec, n->nw};
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int), 4, f) == 4 &&
+              std::fwrite(w.data(), sizeof(double), w.size(), f) == w.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? HISQ_OK : set_error(n->ctx, HISQ_EINVAL, "hisq_net_save: write failed");
+}
+
+int hisq_net_load(hisq_ctx *ctx, const char *path, hisq_net **out)
+{
+    if (!ctx || !path || !out) return HISQ_EINVAL;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return set_error(ctx, HISQ_EINVAL, "hisq_net_load: cannot open file");
+    char magic[8];
+    int hdr[4];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "HISQNET1", 8) == 0 &&
+              std::fread(hdr, sizeof(int), 4, f) == 4;
+    hisq_net_opts o;
+    hisq_net_opts_default(&o);
+    std::vector<double> w;
+    if (ok) {
+        o.nlayer = hdr[0];
+        o.channels = hdr[1];
+        o.link_prec = hdr[2];
+        w.resize(2 * (size_t)std::max(hdr[3], 0));
+        ok = std::fread(w.data(), sizeof(double), w.size(), f) == w.size();
+    }
+    std::fclose(f);
+    if (!ok) return set_error(ctx, HISQ_EINVAL, "hisq_net_load: bad file");
+    int rc = hisq_net_create(ctx, &o, out);
+    if (rc) return rc;
+    if ((long)w.size() != 2 * (*out)->nw) {
+        hisq_net_destroy(*out);
+        *out = nullptr;
+        return set_error(ctx, HISQ_EINVAL, "hisq_net_load: weight count mismatch");
+    }
+    return hisq_net_set_weights(*out, w.data());
+}
+
+int hisq_fcg(hisq_ctx *ctx, double m, hisq_net *net, const double *b, double *x, const hisq_solve_opts *opts,
+             hisq_stats *stats)
+{
+    if (!ctx) return HISQ_EINVAL;
+    if (!b || !x || !(m >= 0.0) || (net && net->ctx != ctx)) return set_error(ctx, HISQ_EINVAL, "hisq_fcg: bad argument");
+    hisq_solve_opts o;
+    if (opts) o = *opts;
+    else hisq_solve_opts_default(&o);
+    const int pa = o.prec_precise == HISQ_F64X ? HISQ_F64X : HISQ_F64;
+    if (!ctx->links[pa].built || !ctx->links[HISQ_F64].built) return set_error(ctx, HISQ_ENOTBUILT, "hisq_fcg: precision");
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    cudaSetDevice(ctx->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    const uint32_t Vh = ctx->g.Vh;
+    const size_t nc = (size_t)Vh * 3; // complex entries
+    const size_t vb = nc * 16, pb = (size_t)ctx->g.VhPad * 48;
+    // workspace: r, rn, z, p, q, t(odd), and float-pair copies for the F64X operator
+    std::vector<void *> mem;
+    auto A = [&](size_t bytes) -> char * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, bytes);
+        mem.push_back(p);
+        return static_cast<char *>(p);
+    };
+    auto release = [&]() {
+        for (void *p : mem) cudaFree(p);
+    };
+    char *r = A(vb), *rn = A(vb), *z = A(vb), *p = A(vb), *q = A(vb), *t = A(vb), *dr = A(vb);
+    char *xx = A(pb), *tx = A(pb), *Ax = A(pb);
+    double *partials = (double *)A(sizeof(double) * 8 * 4096);
+    unsigned *counter = (unsigned *)A(64);
+    Scalars *sc = (Scalars *)A(sizeof(Scalars) * 4);
+    int *bad = (int *)A(sizeof(int));
+    if (!r || !rn || !z || !p || !q || !t || !dr || !xx || !tx || !Ax || !partials || !counter || !sc || !bad) {
+        release();
+        return set_error(ctx, HISQ_ENOMEM, "hisq_fcg: workspace");
+    }
+    Scalars hsc[4];
+    cudaStream_t st = (cudaStream_t)o.stream;
+    const int nblk = (int)std::min<size_t>((Vh + kVecBlock - 1) / kVecBlock, 4ull * ctx->sm_count);
+    Reduce R;
+    R.partials = partials;
+    R.counter = counter;
+    R.sc = sc;
+    R.nblocks = nblk;
+    R.ntotal = nblk;
+    auto dot = [&](const char *a, const char *c, double &re, double &im) -> int {
+        Reduce Q = R;
+        Q.op = FIN_CDOT;
+        k_cdot<HISQ_F64><<<nblk, kVecBlock, 0, st>>>(VecRef{(char *)a, 0}, VecRef{(char *)c, 0}, Vh, Q);
+        if (cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return cuda_error(ctx, cudaGetLastError(), "hisq_fcg: reduction");
+        re = hsc[0].last;
+        im = hsc[0].last_im;
+        return HISQ_OK;
+    };
+    auto applyA = [&](int prec, const char *in, char *out) -> int {
+        if (prec == HISQ_F64) return apply_mdagm(ctx, HISQ_F64, m, in, t, out, 1, nc * 16, st, nullptr, true);
+        k_convert<HISQ_F64, HISQ_F64X><<<nblk, kVecBlock, 0, st>>>(VecRef{(char *)in, 0}, VecRef{xx, 0}, Vh);
+        int rc = apply_mdagm(ctx, HISQ_F64X, m, xx, tx, Ax, 1, pb, st, nullptr, true);
+        if (rc) return rc;
+        k_convert<HISQ_F64X, HISQ_F64><<<nblk, kVecBlock, 0, st>>>(VecRef{Ax, 0}, VecRef{out, 0}, Vh);
+        return HISQ_OK;
+    };
+    const int gb = (int)std::min<size_t>((nc + 255) / 256, 8ull * ctx->sm_count);
+    bool use_net = net != nullptr;
+    int fallbacks = 0;
+    auto precond = [&](const char *in, char *out) -> int {
+        if (use_net) {
+            int rc = net_forward(net, (const double *)in, (double *)out, st);
+            if (rc) return rc;
+            cudaMemsetAsync(bad, 0, sizeof(int), st);
+            k_finite<<<gb, 256, 0, st>>>((const double *)out, nc * 2, bad);
+            int hb = 0;
+            cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+            cudaStreamSynchronize(st);
+            if (!hb) return HISQ_OK;
+            use_net = false;
+            fallbacks++;
+        }
+        return cudaMemcpyAsync(out, in, vb, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? HISQ_OK
+                                                                                            : cuda_error(ctx, cudaErrorUnknown, "copy");
+    };
+    int rc = HISQ_OK;
+    double bb, tmp;
+    if (o.zero_guess) cudaMemsetAsync(x, 0, vb, st);
+    if ((rc = dot((const char *)b, (const char *)b, bb, tmp))) { release(); return rc; }
+    // r = b - A x
+    if ((rc = applyA(pa, (const char *)x, q))) { release(); return rc; }
+    k_sub<<<gb, 256, 0, st>>>((const double2 *)b, (const double2 *)q, (double2 *)r, nc);
+    if ((rc = precond(r, z))) { release(); return rc; }
+    cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, st);
+    double rz_re, rz_im, rr;
+    if ((rc = dot(r, z, rz_re, rz_im)) || (rc = dot(r, r, rr, tmp))) { release(); return rc; }
+    int it = 0, since_best = 0;
+    double best = rr;
+    const double stop = o.tol * o.tol * bb;
+    bool converged = !(rr > stop);
+    while (!converged && it < o.maxiter) {
+        if ((rc = applyA(pa, p, q))) break;
+        double pq, pq_im;
+        if ((rc = dot(p, q, pq, pq_im))) break;
+        if (!(pq > 0.0)) { rc = HISQ_ENOTCONVERGED; break; }
+        // alpha = <r,z> / <p,Ap>
+        const double ar = rz_re / pq, ai = rz_im / pq;
+        k_fcg_update<<<gb, 256, 0, st>>>((double2 *)x, (const double2 *)p, (const double2 *)q, (const double2 *)r,
+                                         (double2 *)rn, nc, ar, ai);
+        it++;
+        if ((rc = dot(rn, rn, rr, tmp))) break;
+        if (rr < best) { best = rr; since_best = 0; }
+        else if (++since_best >= 50 && use_net) { use_net = false; fallbacks++; since_best = 0; }
+        if (rr <= stop) {
+            // confirm with the FP64 operator
+            if ((rc = applyA(HISQ_F64, (const char *)x, q))) break;
+            k_sub<<<gb, 256, 0, st>>>((const double2 *)b, (const double2 *)q, (double2 *)rn, nc);
+            double rt;
+            if ((rc = dot(rn, rn, rt, tmp))) break;
+            if (rt <= stop) { rr = rt; converged = true; break; }
+            rr = rt; // restart from the true residual
+            std::swap(r, rn);
+            if ((rc = precond(r, z))) break;
+            cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, st);
+            if ((rc = dot(r, z, rz_re, rz_im))) break;
+            continue;
+        }
+        if ((rc = precond(rn, z))) break;
+        // beta = <r' - r, z'> / <r, z>
+        k_sub<<<gb, 256, 0, st>>>((const double2 *)rn, (const double2 *)r, (double2 *)dr, nc);
+        double nr, ni;
+        if ((rc = dot(dr, z, nr, ni))) break;
+        const double den = rz_re * rz_re + rz_im * rz_im;
+        const double br = (nr * rz_re + ni * rz_im) / den, bi = (ni * rz_re - nr * rz_im) / den;
+        k_fcg_p<<<gb, 256, 0, st>>>((double2 *)p, (const double2 *)z, nc, br, bi);
+        std::swap(r, rn);
+        if ((rc = dot(r, z, rz_re, rz_im))) break;
+    }
+    cudaStreamSynchronize(st);
+    release();
+    if (stats) {
+        stats->iterations = it;
+        stats->reliable_updates = fallbacks;
+        stats->true_residual = std::sqrt(rr / bb);
+        stats->iterated_residual = std::sqrt(rr / bb);
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        stats->dslash_calls = 2L * (it + 2);
+    }
+    if (rc && rc != HISQ_ENOTCONVERGED) return rc;
+    if (!converged) return set_error(ctx, HISQ_ENOTCONVERGED, "hisq_fcg: tolerance not reached");
+    return HISQ_OK;
+}
+
+}  // extern "C"

@@ -54,6 +54,13 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class NetOpts(ctypes.Structure):
+    _fields_ = [("nlayer", ctypes.c_int), ("channels", ctypes.c_int), ("link_prec", ctypes.c_int),
+                ("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("init_hop", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+
+
 _P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
 
 _SIGS = {
@@ -77,6 +84,18 @@ _SIGS = {
     "hisq_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "hisq_cg": (_I, [_P, _D, _P, _P, _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
     "hisq_multishift_cg": (_I, [_P, _D, _I, _P, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
+    "hisq_net_opts_default": (None, [ctypes.POINTER(NetOpts)]),
+    "hisq_net_create": (_I, [_P, ctypes.POINTER(NetOpts), ctypes.POINTER(_P)]),
+    "hisq_net_destroy": (None, [_P]),
+    "hisq_net_num_weights": (_L, [_P]),
+    "hisq_net_get_weights": (_I, [_P, _P]),
+    "hisq_net_set_weights": (_I, [_P, _P]),
+    "hisq_net_apply": (_I, [_P, _P, _P, _P]),
+    "hisq_net_loss_grad": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
+    "hisq_net_train": (_I, [_P, _I, _P, _P, _P]),
+    "hisq_net_save": (_I, [_P, ctypes.c_char_p]),
+    "hisq_net_load": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_P)]),
+    "hisq_fcg": (_I, [_P, _D, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats)]),
 }
 
 
@@ -207,6 +226,83 @@ class Context:
         rc = self.check(lib().hisq_multishift_cg(self.h, float(m), n, sig, _ptr(b), xp, tp, ctypes.byref(o),
                                                  ctypes.byref(st), _ptr(residuals)))
         return rc, st
+
+
+class Net:
+    """Learned preconditioner (hisq_net_*): gauge-covariant parallel-transport network."""
+
+    def __init__(self, ctx: Context, handle=None, **opts):
+        self.ctx = ctx
+        if handle is not None:
+            self.h = handle
+        else:
+            o = NetOpts()
+            lib().hisq_net_opts_default(ctypes.byref(o))
+            for k, v in opts.items():
+                setattr(o, k, v)
+            h = ctypes.c_void_p()
+            ctx.check(lib().hisq_net_create(ctx.h, ctypes.byref(o), ctypes.byref(h)))
+            self.h = h
+        self.nw = lib().hisq_net_num_weights(self.h)
+
+    @classmethod
+    def load(cls, ctx: Context, path: str):
+        h = ctypes.c_void_p()
+        ctx.check(lib().hisq_net_load(ctx.h, path.encode(), ctypes.byref(h)))
+        return cls(ctx, handle=h)
+
+    def save(self, path: str):
+        self.ctx.check(lib().hisq_net_save(self.h, path.encode()))
+
+    def get_weights(self):
+        import numpy as np
+        w = np.zeros(2 * self.nw)
+        self.ctx.check(lib().hisq_net_get_weights(self.h, w.ctypes.data_as(ctypes.c_void_p)))
+        return w[0::2] + 1j * w[1::2]
+
+    def set_weights(self, w):
+        import numpy as np
+        w = np.asarray(w, dtype=np.complex128).ravel()
+        a = np.ascontiguousarray(np.stack([w.real, w.imag], axis=1).ravel())
+        self.ctx.check(lib().hisq_net_set_weights(self.h, a.ctypes.data_as(ctypes.c_void_p)))
+
+    def apply(self, b, z, stream=None):
+        self.ctx.check(lib().hisq_net_apply(self.h, _ptr(b), _ptr(z), _stream(stream)))
+
+    def loss_grad(self, b, x):
+        import numpy as np
+        loss = ctypes.c_double()
+        g = np.zeros(2 * self.nw)
+        self.ctx.check(lib().hisq_net_loss_grad(self.h, _ptr(b), _ptr(x), ctypes.byref(loss),
+                                                 g.ctypes.data_as(ctypes.c_void_p)))
+        return loss.value, g[0::2] + 1j * g[1::2]
+
+    def train(self, B, X, epochs):
+        import numpy as np
+        losses = np.zeros(max(epochs, 1))
+        npairs = B.shape[0]
+        self.ctx.check(lib().hisq_net_train(self.h, npairs, _ptr(B), _ptr(X), losses.ctypes.data_as(ctypes.c_void_p)))
+        return losses[:epochs]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hisq_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fcg(ctx: Context, m, b, x, net=None, opts=None, **kw):
+    """Flexible CG with the network preconditioner (hisq_fcg)."""
+    o = opts or ctx.solve_opts(**kw)
+    st = Stats()
+    rc = ctx.check(lib().hisq_fcg(ctx.h, float(m), net.h if net is not None else None, _ptr(b), _ptr(x),
+                                  ctypes.byref(o), ctypes.byref(st)))
+    return rc, st
 
 
 class Field:

@@ -1,0 +1,119 @@
+"""GPU learned preconditioner (through the C ABI) against the FP64 oracle.
+
+Activations are stored in BF16 (unit roundoff 2^-8); with FP32 arithmetic and four layers
+the network output is compared norm-wise within 3e-2 of the oracle's FP64 forward pass,
+the loss within 3e-2 and the weight gradient within 6e-2 (norm-wise).  Flexible CG with the
+network must reach a true FP64 residual <= 1e-10 (recomputed by the oracle).
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from hisq_inputs import fields
+
+hisq = pytest.importorskip("paper_2306_01098_gb300.hisq")
+
+pytestmark = pytest.mark.gpu
+
+NTAP = 17
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def rand_weights(chans, seed, scale=0.4):
+    rng = np.random.default_rng(seed)
+    ws = []
+    for l in range(len(chans) - 1):
+        n = NTAP * chans[l + 1] * chans[l]
+        w = scale * (rng.normal(size=n) + 1j * rng.normal(size=n)) / np.sqrt(NTAP * chans[l])
+        ws.append(w)
+    return np.concatenate(ws)
+
+
+@pytest.fixture(scope="module")
+def small():
+    dims = (6, 4, 4, 6)
+    fat, lng = fields.recipe_links(dims, 0.5, 77)
+    ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=(hisq.F64, hisq.F64X, hisq.F32, hisq.F16))
+    return dims, ctx, fat.numpy(), lng.numpy()
+
+
+@pytest.mark.parametrize("link_prec,tol", [(hisq.F32, 3e-2), (hisq.F16, 3e-2)])
+def test_network_forward_matches_oracle(small, link_prec, tol):
+    dims, ctx, fat, lng = small
+    net = hisq.Net(ctx, link_prec=link_prec)
+    chans = [1, 8, 8, 8, 1]
+    w = rand_weights(chans, 5)
+    assert w.size == net.nw
+    net.set_weights(w)
+    b = fields.gaussian_source(dims, 300)[0]
+    z = torch.empty_like(b).cuda()
+    net.apply(b.cuda(), z)
+    want = oracle.net_apply(dims, fat, lng, chans, w, b.numpy())
+    assert rel(z.cpu().numpy(), want) <= tol
+
+
+def test_network_loss_and_gradient_match_oracle(small):
+    dims, ctx, fat, lng = small
+    net = hisq.Net(ctx)
+    chans = [1, 8, 8, 8, 1]
+    w = rand_weights(chans, 6)
+    net.set_weights(w)
+    b = fields.gaussian_source(dims, 301)[0]
+    x = fields.gaussian_source(dims, 302)[0]
+    loss, g = net.loss_grad(b.cuda(), x.cuda())
+    loss_o, g_o = oracle.net_loss_grad(dims, fat, lng, chans, w, b.numpy(), x.numpy())
+    assert abs(loss - loss_o) <= 3e-2 * loss_o
+    assert rel(g, g_o) <= 6e-2
+    # per layer as well: no layer's gradient may be wrong while the total norm looks fine
+    off = 0
+    for l in range(4):
+        n = NTAP * chans[l + 1] * chans[l]
+        assert rel(g[off:off + n], g_o[off:off + n]) <= 8e-2, l
+        off += n
+
+
+def test_weights_roundtrip_and_save_load(small, tmp_path):
+    dims, ctx, fat, lng = small
+    net = hisq.Net(ctx, channels=4)
+    w = rand_weights([1, 4, 4, 4, 1], 7)
+    net.set_weights(w)
+    assert np.abs(net.get_weights() - w).max() < 1e-6 * np.abs(w).max()
+    p = str(tmp_path / "net.bin")
+    net.save(p)
+    net2 = hisq.Net.load(ctx, p)
+    assert np.array_equal(net2.get_weights(), net.get_weights())
+
+
+def test_training_lowers_loss_and_fcg_converges():
+    dims, m = (8, 8, 8, 8), 0.05
+    fat, lng = fields.recipe_links(dims, 0.5, 78)
+    ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=(hisq.F64, hisq.F64X, hisq.F32, hisq.F16))
+    npairs = 32
+    B = fields.gaussian_source(dims, 310, npairs).cuda()
+    X = torch.zeros_like(B)
+    for k in range(0, npairs, 8):
+        rc, st = ctx.cg(m, B[k:k + 8].contiguous(), X[k:k + 8], tol=1e-8, prec_sloppy=hisq.F32, prec_precise=hisq.F64)
+        assert rc == hisq.OK
+    X = X.contiguous()
+    net = hisq.Net(ctx, epochs=4, batch=4, lr=3e-3)
+    losses = net.train(B, X, 4)
+    assert np.all(np.isfinite(losses)) and losses[-1] < losses[0]
+    b = fields.gaussian_source(dims, 320)[0]
+    x = torch.zeros_like(b).cuda()
+    rc, st = hisq.fcg(ctx, m, b.cuda(), x, net=net, tol=1e-10, prec_precise=hisq.F64X)
+    assert rc == hisq.OK
+    r = b.numpy() - oracle.mdagm(dims, fat.numpy(), lng.numpy(), m, x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(b.numpy()) <= 1e-10
+    # without a network flexible CG is CG
+    x0 = torch.zeros_like(b).cuda()
+    rc0, st0 = hisq.fcg(ctx, m, b.cuda(), x0, net=None, tol=1e-10, prec_precise=hisq.F64)
+    xc = torch.zeros_like(b).cuda()
+    rcc, stc = ctx.cg(m, b.cuda(), xc, tol=1e-10, prec_sloppy=hisq.F64)
+    assert rc0 == hisq.OK and abs(st0.iterations - stc.iterations) <= 2
+    print(f"losses {losses}, FCG(net) {st.iterations} iterations, FCG(1) {st0.iterations}, CG {stc.iterations}")
