@@ -227,20 +227,24 @@ __global__ void __launch_bounds__(kVecBlock) k_accum_hi(VecRef xhi, VecRef xlo, 
     }
 }
 
-// r (F64) = b (F64) - Ax (PA); |r|^2 reduced (FIN_STORE -> Scalars.last)
+// r (F64) = b (F64) - Ax (PA) [- shift_rhs x (F64)]; |r|^2 reduced (FIN_STORE -> Scalars.last)
 template <int PA>
-__global__ void __launch_bounds__(kVecBlock) k_residual(VecRef b, VecRef Ax, VecRef r, uint32_t Vh, Reduce red)
+__global__ void __launch_bounds__(kVecBlock) k_residual(VecRef b, VecRef Ax, VecRef r, uint32_t Vh, Reduce red,
+                                                        const double *shift = nullptr, VecRef x = VecRef{nullptr, 0})
 {
     const int rhs = blockIdx.y;
+    const double sh = shift ? shift[rhs] : 0.0;
     double acc = 0.0;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
-        typename Blas<HISQ_F64>::Vec bv, rv;
+        typename Blas<HISQ_F64>::Vec bv, rv, xv;
         typename Blas<PA>::Vec av;
         vload<HISQ_F64>(b.rhs(rhs), s, bv);
         vload<PA>(Ax.rhs(rhs), s, av);
+        if (sh != 0.0) vload<HISQ_F64>(x.rhs(rhs), s, xv);
 #pragma unroll
         for (int i = 0; i < 6; i++) {
             rv.v[i] = bv.v[i] - Blas<PA>::get(av, i);
+            if (sh != 0.0) rv.v[i] -= sh * xv.v[i];
             acc = fma(rv.v[i], rv.v[i], acc);
         }
         Blas<HISQ_F64>::store(r.rhs(rhs), s, rv);

@@ -144,6 +144,8 @@ void SolverWork::release()
     prof.clear();
     if (h_sc) cudaFreeHost(h_sc);
     h_sc = nullptr;
+    if (h_shift) cudaFreeHost(h_shift);
+    h_shift = nullptr;
     if (st) cudaStreamDestroy(st);
     st = nullptr;
     if (ev) cudaEventDestroy(ev);
@@ -226,8 +228,12 @@ int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out)
     W.counter = reinterpret_cast<unsigned *>(tmp);
     A(&tmp, sizeof(LoopCtl));
     W.ctl = reinterpret_cast<LoopCtl *>(tmp);
+    A(&tmp, sizeof(double) * (nrhs + 64));
+    W.shift_buf = reinterpret_cast<double *>(tmp);
     if (rc) return rc;
-    if (cudaMallocHost(&W.h_sc, sizeof(Scalars) * (nrhs + 64)) != cudaSuccess) return set_error(ctx, HISQ_ENOMEM, "pinned scalars");
+    if (cudaMallocHost(&W.h_sc, sizeof(Scalars) * (nrhs + 64)) != cudaSuccess ||
+        cudaMallocHost(&W.h_shift, sizeof(double) * (nrhs + 64)) != cudaSuccess)
+        return set_error(ctx, HISQ_ENOMEM, "pinned scalars");
     if (cudaStreamCreateWithFlags(&W.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&W.ev, cudaEventDisableTiming) != cudaSuccess)
         return set_error(ctx, HISQ_ECUDA, "solver stream");
@@ -311,6 +317,7 @@ static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream
     b.skip = w.sc;
     b.pv = w.p;
     b.m4 = 4.0 * m * m;
+    b.shift = w.shift;
     const int gx = (int)(((size_t)w.Vh * w.shape.ds + kDslashBlock - 1) / kDslashBlock); // blocks along x
     b.red = w.red(FIN_ALPHA, gx, gx * (w.nrhs / nr));
     if (evs) cudaEventRecord(evs[2], st);
@@ -389,12 +396,14 @@ int precise_residual(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, in
     if (prec == HISQ_F64) {
         if ((rc = apply_mdagm(ctx, HISQ_F64, m, w.x64, w.thi, w.Axhi, w.nrhs, w.rb64, st, nullptr, true))) return rc;
         k_residual<HISQ_F64><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axhi, w.rb64}, VecRef{w.rhi, w.rb64},
-                                                     w.Vh, w.red(FIN_STORE, w.nblk_vec));
+                                                     w.Vh, w.red(FIN_STORE, w.nblk_vec), w.shift,
+                                                     VecRef{w.x64, w.rb64});
     } else {
         k_convert<HISQ_F64, HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.x64, w.rb64}, VecRef{w.xx, w.rbP}, w.Vh);
         if ((rc = apply_mdagm(ctx, HISQ_F64X, m, w.xx, w.tx, w.Axx, w.nrhs, w.rbP, st, nullptr, true))) return rc;
         k_residual<HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axx, w.rbP}, VecRef{w.rhi, w.rb64},
-                                                      w.Vh, w.red(FIN_STORE, w.nblk_vec));
+                                                      w.Vh, w.red(FIN_STORE, w.nblk_vec), w.shift,
+                                                      VecRef{w.x64, w.rb64});
     }
     HISQ_CUDA(ctx, cudaGetLastError());
     return HISQ_OK;
@@ -408,8 +417,9 @@ static int read_scalars(hisq_ctx *ctx, SolverWork &w, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------- the solve
+// shifts (host, may be NULL): per right-hand side sigma, solving (A + sigma_k) x_k = b_k
 int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const hisq_solve_opts &o, hisq_stats *stats,
-           double *residuals)
+           double *residuals, const double *shifts)
 {
     const double t0 = wall();
     int ps = o.prec_sloppy, pp = o.prec_precise;
@@ -430,6 +440,16 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
     if (o.zero_guess) HISQ_CUDA(ctx, cudaMemsetAsync(w.x64, 0, vb, st));
     else HISQ_CUDA(ctx, cudaMemcpyAsync(w.x64, x, vb, k_in, st));
     HISQ_CUDA(ctx, cudaMemsetAsync(w.xlo, 0, w.rbX * nrhs, st));
+    // per right-hand side shifts (the operator's m4 + sigma_k in the epilogue and residuals)
+    if (shifts) {
+        std::memcpy(w.h_shift, shifts, sizeof(double) * nrhs);
+        HISQ_CUDA(ctx, cudaMemcpyAsync(w.shift_buf, w.h_shift, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+        w.shift = w.shift_buf;
+        w.shift_key = std::vector<double>(shifts, shifts + nrhs);
+    } else {
+        w.shift = nullptr;
+        w.shift_key.clear();
+    }
     const dim3 g(w.nblk_vec, nrhs);
     const double tol2 = o.tol * o.tol;
     const double delta2 = o.reliable_delta * o.reliable_delta;
@@ -495,10 +515,11 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
                 if ((rc = launch_iteration(ctx, w, m, st, &w.prof[0], 0))) return rc;
                 kernels += 4;
             }
-            if (!w.graph || w.graph_m != m || w.graph_l2 != (win.num_bytes > 0)) {
+            if (!w.graph || w.graph_m != m || w.graph_l2 != (win.num_bytes > 0) || w.graph_shift != w.shift_key) {
                 if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
                 if ((rc = build_loop_graph(ctx, w, m, win, st))) return rc;
                 w.graph_m = m;
+                w.graph_shift = w.shift_key;
                 w.graph_l2 = win.num_bytes > 0;
             }
             HISQ_CUDA(ctx, cudaGraphLaunch(w.graph, st));
@@ -636,7 +657,7 @@ int hisq_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const
     if (!(o.tol > 0.0) || o.maxiter < 1) return set_error(ctx, HISQ_EINVAL, "hisq_cg: bad tolerance or maxiter");
     if (stats) std::memset(stats, 0, sizeof(*stats));
     cudaSetDevice(ctx->device);
-    return run_cg(ctx, m, b, x, nrhs, o, stats, residuals);
+    return run_cg(ctx, m, b, x, nrhs, o, stats, residuals, nullptr);
 }
 
 }  // extern "C"

@@ -22,6 +22,7 @@ struct DslashArgs {
     // normal-operator epilogue: out = m4 * pv - D in, <pv, out> reduced
     const char *pv;
     double m4;
+    const double *shift;   // optional per right-hand side addition to m4 (device)
     Reduce red;
 };
 

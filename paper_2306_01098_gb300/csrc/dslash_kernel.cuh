@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
             if constexpr (EPI == 1) {
                 typename T::Vec pv;
                 T::load(a.pv + (size_t)(rhs0 + r) * a.rhs_bytes, s, pv);
-                T::mdagm_epilogue(out[r], a.m4, pv);
+                T::mdagm_epilogue(out[r], a.shift ? a.m4 + a.shift[rhs0 + r] : a.m4, pv);
                 dots[r] = T::dot(pv, out[r]);
             }
             T::store(a.out + (size_t)(rhs0 + r) * a.rhs_bytes, s, out[r]);

@@ -1,17 +1,18 @@
 // multishift.cu -- multi-shift CG (Sec. 3.2 and its reference to Jegerlehner): solves
 // (A + sigma_s) x_s = b for all shifts with one operator application per iteration, on the
 // smallest shift sigma_0; the other shifts follow from the shift invariance of the Krylov
-// space at the cost of one fused vector update per iteration:
+// space at the cost of one fused vector update per iteration (for every shift):
 //   q = (A + sigma_0) p_0,  alpha = |r|^2 / <p_0, q>                  (Dslash pair + epilogue)
 //   r -= alpha q,  beta = |r_new|^2 / |r|^2                          (fused update + norm)
 //   zeta_s' = zeta_s zeta_s^- alpha^- /
 //             [alpha^- zeta_s^- (1 + alpha d_s) + alpha beta^- (zeta_s^- - zeta_s)]
 //   alpha_s = alpha zeta_s' / zeta_s,  beta_s = beta (zeta_s' / zeta_s)^2     (one thread per shift)
 //   x_s += alpha_s p_s,  p_s = zeta_s' r + beta_s p_s                (one pass, all shifts)
-// with d_s = sigma_s - sigma_0; shift s stops once |zeta_s| |r| <= tol_s |b|.  In a reduced
-// sloppy precision each shift is afterwards finished by the mixed-precision CG of cg.cu on
-// A + sigma_s = 4 m_s^2 - D_eo D_oe, m_s = sqrt(m^2 + sigma_s / 4), started from x_s; in FP64
-// that step only recomputes and confirms the residual.
+// with d_s = sigma_s - sigma_0; shift s stops once |zeta_s| |r| <= tol_s |b|.  Afterwards all
+// shifts are finished together by one multi-right-hand-side CG of cg.cu with a per-right-hand-
+// side shift (A + sigma_s) x_s = b started from the multi-shift iterates, so the links are read
+// once per iteration for every shift; in a reduced sloppy precision this is a mixed-precision
+// solve with FP64 reliable updates, in FP64 it only recomputes and confirms the residuals.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -26,7 +27,7 @@
 namespace hisq {
 
 int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const hisq_solve_opts &o, hisq_stats *stats,
-           double *residuals);
+           double *residuals, const double *shifts);
 
 constexpr int kMaxShift = 64;
 
@@ -44,6 +45,7 @@ struct MsWork {
     uint32_t Vh = 0;
     size_t rbS = 0, rbX = 0, rb64 = 0;
     char *r = nullptr, *q = nullptr, *t = nullptr, *p = nullptr, *x = nullptr, *b64 = nullptr;
+    char *ball = nullptr, *xall = nullptr; // [nshift][Vh] FP64: b repeated, iterates (refinement)
     Scalars *sc = nullptr, *h_sc = nullptr;
     ShiftState *ss = nullptr, *h_ss = nullptr;
     double *partials = nullptr;
@@ -247,6 +249,8 @@ static int get_ms_work(hisq_ctx *ctx, int nshift, int ps, MsWork **out)
     A(&W.p, W.rbS * nshift);
     A(&W.x, W.rbX * nshift);
     A(&W.b64, W.rb64);
+    A(&W.ball, W.rb64 * nshift);
+    A(&W.xall, W.rb64 * nshift);
     char *tmp = nullptr;
     A(&tmp, sizeof(Scalars) * 4);
     W.sc = reinterpret_cast<Scalars *>(tmp);
@@ -391,28 +395,37 @@ extern "C" int hisq_multishift_cg(hisq_ctx *ctx, double m, int nshift, const dou
     HISQ_CUDA(ctx, cudaStreamSynchronize(st));
     if (bad) return set_error(ctx, HISQ_ENOTCONVERGED, "hisq_multishift_cg: non-finite residual");
 
-    // confirm (FP64) or finish (reduced precision) every shift with CG from its iterate
+    // finish every shift together: multi-RHS CG on (A + sigma_s) x_s = b from the iterates
     hisq_solve_opts co = o;
     co.zero_guess = 0;
     co.host_buffers = 0;
     co.stream = nullptr;
     if (ps == HISQ_F64 || ps == HISQ_F64X) co.prec_precise = ps;
-    int worst_rc = HISQ_OK, extra = 0, nru = 0;
-    double worst = 0.0;
+    double tmin_all = o.tol;
+    std::vector<double> shifts(nshift);
     for (int k = 0; k < nshift; k++) {
         const int s = order[k];
-        co.tol = tol ? tol[s] : o.tol;
-        const double ms = std::sqrt(m * m + sigma[s] / 4.0);
-        hisq_stats cs{};
-        double res = 0.0;
-        int r2 = run_cg(ctx, ms, b, x[s], 1, co, &cs, &res);
-        if (r2 != HISQ_OK && r2 != HISQ_ENOTCONVERGED) return r2;
-        if (r2 != HISQ_OK) worst_rc = r2;
-        if (residuals) residuals[s] = res;
-        worst = std::max(worst, res);
-        extra += cs.iterations;
-        nru += cs.reliable_updates;
+        if (tol) tmin_all = std::min(tmin_all, tol[s]);
+        shifts[k] = sigma[s];
+        HISQ_CUDA(ctx, cudaMemcpyAsync(w.ball + k * w.rb64, b, w.rb64, cudaMemcpyDeviceToDevice, st));
+        HISQ_CUDA(ctx, cudaMemcpyAsync(w.xall + k * w.rb64, x[s], w.rb64, cudaMemcpyDeviceToDevice, st));
     }
+    co.tol = tmin_all;
+    HISQ_CUDA(ctx, cudaStreamSynchronize(st));
+    hisq_stats cs{};
+    std::vector<double> res(nshift, 0.0);
+    const int r2 = run_cg(ctx, m, (const double *)w.ball, (double *)w.xall, nshift, co, &cs, res.data(), shifts.data());
+    if (r2 != HISQ_OK && r2 != HISQ_ENOTCONVERGED) return r2;
+    int worst_rc = r2;
+    for (int k = 0; k < nshift; k++)
+        HISQ_CUDA(ctx, cudaMemcpyAsync(x[order[k]], w.xall + k * w.rb64, w.rb64, cudaMemcpyDeviceToDevice, st));
+    HISQ_CUDA(ctx, cudaStreamSynchronize(st));
+    double worst = 0.0;
+    for (int k = 0; k < nshift; k++) {
+        if (residuals) residuals[order[k]] = res[k];
+        worst = std::max(worst, res[k]);
+    }
+    const int extra = cs.iterations, nru = cs.reliable_updates;
     if (stats) {
         stats->iterations = ms_iters + extra;
         stats->reliable_updates = nru;

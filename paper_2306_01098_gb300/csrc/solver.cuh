@@ -21,6 +21,9 @@ struct SolverWork {
     double *partials = nullptr;
     unsigned *counter = nullptr;
     LoopCtl *ctl = nullptr;  // device-side loop control
+    double *shift_buf = nullptr, *h_shift = nullptr; // per right-hand side shifts (device, pinned host)
+    const double *shift = nullptr;                   // shift_buf when shifts are in use
+    std::vector<double> shift_key, graph_shift;      // shifts the loop graph was captured with
     int nblk_vec = 0, nblk_dslash = 0;
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;

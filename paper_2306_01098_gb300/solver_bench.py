@@ -43,7 +43,7 @@ def batched(reps=2):
     from paper_2306_01098_gb300 import hisq
     w = workloads.BATCH_64x16
     fat, lng = fields.recipe_links(w.dims, w.eps, w.link_seed, device="cuda")
-    ctx = hisq.Context(w.dims, fat, lng, precs=(hisq.F64, hisq.F32, hisq.F16))
+    ctx = hisq.Context(w.dims, fat, lng, precs=(hisq.F64, hisq.F64X, hisq.F32, hisq.F16))
     del fat, lng
     torch.cuda.empty_cache()
     rows = []
@@ -63,11 +63,12 @@ def batched(reps=2):
                      "iterations": st.iterations, "reliable_updates": st.reliable_updates,
                      "max_true_residual": float(res.max()), "speedup_per_rhs_vs_fp64": ms64 / (ms / nrhs), "rc": rc})
     sig = list(w.shifts)
-    for prec, name in ((hisq.F64, "f64"), (hisq.F16, "f16")):
+    for prec, name in ((hisq.F64, "f64"), (hisq.F64X, "f64x"), (hisq.F16, "f16")):
         xs = [torch.zeros_like(b1[0]) for _ in sig]
         res = torch.zeros(len(sig), dtype=torch.float64)
         ms, (rc, st) = _timed(lambda: ctx.multishift_cg(w.mass, sig, b1[0].contiguous(), xs, tol=[w.tol] * len(sig),
-                                                        prec_sloppy=prec, prec_precise=hisq.F64, residuals=res), reps)
+                                                        prec_sloppy=prec, prec_precise=hisq.F64, reliable_delta=0.01,
+                                                        residuals=res), reps)
         rows.append({"solve": "multishift", "nshift": len(sig), "sloppy": name, "ms": ms, "iterations": st.iterations,
                      "max_true_residual": float(res.max()), "rc": rc})
     ctx.close()
