@@ -150,10 +150,14 @@ int hisq_mdagm_noalloc(hisq_ctx *ctx, double m, const double *in, double *out, i
 
 /* Fix the Dslash launch shape for (link precision, vector precision, nrhs) instead of the
  * autotuner's choice: n_inner right-hand sides per thread (1, 2, 4, 8; at most 4 for F64 and
- * F64X; must divide nrhs) and threads_per_site (1, 2, 4: the four directions are split over
- * that many threads).  Vector precision equals the link precision, or is HISQ_F32 with
- * 16-bit links.  Results do not depend on the shape beyond rounding order. */
-int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int n_inner, int threads_per_site);
+ * F64X; must divide nrhs), threads_per_site (1, 2, 4: the four directions are split over
+ * that many threads) and site_order, the order in which blocks visit the sites: 0 storage
+ * order (t slowest), 1 z and t interchanged (allowed when Nt < Nz and one z-t plane,
+ * Nx/2 * Ny sites, is a multiple of 32), -1 the size-based default.  Vector precision equals
+ * the link precision, or is HISQ_F32 with 16-bit links.  Results do not depend on the shape
+ * beyond the rounding order of the reductions.  Returns HISQ_EINVAL for any other value. */
+int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int n_inner, int threads_per_site,
+                  int site_order);
 
 /* ------------------------------------------------------------------ solvers */
 typedef struct {
@@ -172,8 +176,11 @@ typedef struct {
     int use_graph;         /* 1 (default): iterations run inside a CUDA graph WHILE node
                               that the device stops when every right-hand side pauses or
                               converges; the host looks at the scalars once per phase      */
-    int profile;           /* 1: time the sloppy Dslash pair of the first iteration of every
-                              block of check_interval iterations with CUDA events            */
+    int profile;           /* 1: time the sloppy Dslash pair of the second iteration of every
+                              phase (graph) or block of check_interval iterations (direct
+                              launches) that can run at least three iterations, with CUDA
+                              events; the first two iterations of such a phase are launched
+                              directly so that the timed launches queue behind the first   */
     int l2_persist;        /* keep the sloppy link field in L2 during the solve (persisting
                               access-policy window on the solver's kernels, within this
                               process's persisting-L2 limit; persisting lines are released

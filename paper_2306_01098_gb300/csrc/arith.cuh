@@ -43,27 +43,61 @@ __device__ __forceinline__ uint32_t ld_nc4(const void *p)
     return r;
 }
 
-// link words of site s in a slot; LB = link bytes
+// the same loads with an L2 eviction-priority policy (createpolicy): data read once per
+// application that should not push reused lines out of L2
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint4 ld_nc16(const void *p, uint64_t pol)
+{
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint2 ld_nc8(const void *p, uint64_t pol)
+{
+    uint2 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;" : "=r"(r.x), "=r"(r.y) : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_nc4(const void *p, uint64_t pol)
+{
+    uint32_t r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+    return r;
+}
+
+// link words of site s in a slot; LB = link bytes.  With `hint`, the loads are marked
+// evict-first in L2.
 template <int LB>
-__device__ __forceinline__ void load_link_words(const char *slot, uint32_t s, uint32_t (&w)[LB / 4])
+__device__ __forceinline__ void load_link_words(const char *slot, uint32_t s, uint32_t (&w)[LB / 4], bool hint = false)
 {
     constexpr int NQ = LB / 16, TB = LB % 16;
+    const uint64_t pol = hint ? l2_evict_first_policy() : 0ull;
     const char *blk = slot + (size_t)(s >> 5) * (32 * LB);
     const uint32_t lane = s & 31;
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
-        uint4 v = ld_nc16(blk + q * 512 + lane * 16);
+        const char *a = blk + q * 512 + lane * 16;
+        uint4 v = hint ? ld_nc16(a, pol) : ld_nc16(a);
         w[4 * q + 0] = v.x;
         w[4 * q + 1] = v.y;
         w[4 * q + 2] = v.z;
         w[4 * q + 3] = v.w;
     }
     if constexpr (TB == 8) {
-        uint2 v = ld_nc8(blk + NQ * 512 + lane * 8);
+        const char *a = blk + NQ * 512 + lane * 8;
+        uint2 v = hint ? ld_nc8(a, pol) : ld_nc8(a);
         w[4 * NQ + 0] = v.x;
         w[4 * NQ + 1] = v.y;
     } else if constexpr (TB == 4) {
-        w[4 * NQ] = ld_nc4(blk + NQ * 512 + lane * 4);
+        const char *a = blk + NQ * 512 + lane * 4;
+        w[4 * NQ] = hint ? ld_nc4(a, pol) : ld_nc4(a);
     }
 }
 

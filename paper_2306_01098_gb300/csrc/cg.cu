@@ -318,8 +318,7 @@ static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream
     b.pv = w.p;
     b.m4 = 4.0 * m * m;
     b.shift = w.shift;
-    const int gx = (int)(((size_t)w.Vh * w.shape.ds + kDslashBlock - 1) / kDslashBlock); // blocks along x
-    b.red = w.red(FIN_ALPHA, gx, gx * (w.nrhs / nr));
+    b.red = w.red(FIN_ALPHA, 0, 0); // block counts filled in by the launcher
     if (evs) cudaEventRecord(evs[2], st);
     e = dslash_launch(w.ps, w.pv, 1, b, L.nreal, w.shape, st);
     if (evs) cudaEventRecord(evs[3], st);
@@ -510,10 +509,16 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         if (!o.use_graph) cap = std::min(cap, ci);
         k_phase_begin<<<1, 1, 0, st>>>(w.ctl, w.sc, cap);
         kernels++;
+        // Sampled timing: the phase's first two iterations run as direct launches and the
+        // second one's Dslash pair is timed; queued behind the first, its launches start
+        // back to back on the GPU, so the events hold no host launch gaps.  Taken only when
+        // the phase may run three or more iterations; kept only if both did work.
+        const bool sample = prof && cap >= 3;
         if (o.use_graph) {
-            if (prof) { // sampled timing: the phase's first iteration runs outside the graph
+            if (sample) {
+                if ((rc = launch_iteration(ctx, w, m, st, nullptr, 0))) return rc;
                 if ((rc = launch_iteration(ctx, w, m, st, &w.prof[0], 0))) return rc;
-                kernels += 4;
+                kernels += 8;
             }
             if (!w.graph || w.graph_m != m || w.graph_l2 != (win.num_bytes > 0) || w.graph_shift != w.shift_key) {
                 if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
@@ -525,13 +530,13 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             HISQ_CUDA(ctx, cudaGraphLaunch(w.graph, st));
         } else {
             for (int i = 0; i < cap; i++)
-                if ((rc = launch_iteration(ctx, w, m, st, (prof && i == 0) ? &w.prof[0] : nullptr, 0))) return rc;
+                if ((rc = launch_iteration(ctx, w, m, st, (sample && i == 1) ? &w.prof[0] : nullptr, 0))) return rc;
         }
         if ((rc = read_scalars(ctx, w, st))) return rc;
         const int executed = w.h_sc[0].it_all - it_all; // iterations the device ran in this phase
         it_all = w.h_sc[0].it_all;
         since_ru += executed;
-        kernels += 4L * executed - (o.use_graph && prof ? 4 : 0);
+        kernels += 4L * executed - (o.use_graph && sample ? 8 : 0);
         int it = 0;
         bool any_active = false, any_flag = false;
         for (int r = 0; r < nrhs; r++) {
@@ -542,7 +547,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         const int ran = it - prev_iters; // iterations that did work
         prev_iters = it;
         dcalls += 2L * ran;
-        if (prof && ran > 0) {
+        if (sample && ran >= 2) {
             for (int j = 0; j < 2; j++) {
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, w.prof[2 * j], w.prof[2 * j + 1]) == cudaSuccess) {

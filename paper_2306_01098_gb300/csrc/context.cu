@@ -361,6 +361,11 @@ int hisq_create(hisq_ctx **out, const int dims[4], const double *fat, const doub
         return HISQ_ECUDA;
     }
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, opts.device);
+    {
+        int maxp = 0;
+        cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, opts.device);
+        ctx->l2_persist_max = maxp > 0 ? (size_t)maxp : 0;
+    }
     Geom &g = ctx->g;
     for (int i = 0; i < 4; i++) g.n[i] = dims[i];
     g.nxh = dims[0] / 2;
@@ -372,6 +377,9 @@ int hisq_create(hisq_ctx **out, const int dims[4], const double *fat, const doub
     g.dx.init(g.nxh);
     g.dy.init(dims[1]);
     g.dz.init(dims[2]);
+    g.dp.init(g.sz);
+    g.dt.init(dims[3]);
+    g.zt_ok = (g.sz % 32u) == 0 && dims[3] < dims[2];
 
     int rc = HISQ_OK;
     const size_t link_doubles = 4ull * V * 18;

@@ -21,17 +21,19 @@ cudaError_t dslash_launch(int pl, int pv, int epi, const DslashArgs &a, int nrea
                           cudaStream_t st)
 {
     const int nr = sh.nr, ds = sh.ds;
+    DslashArgs b = a;
+    b.zt = sh.order;
     if (pl == pv) {
         switch (pl) {
-        case HISQ_F64: return dslash_launch_HISQ_F64_HISQ_F64(epi, a, nreal, nr, ds, st);
-        case HISQ_F64X: return dslash_launch_HISQ_F64X_HISQ_F64X(epi, a, nreal, nr, ds, st);
-        case HISQ_F32: return dslash_launch_HISQ_F32_HISQ_F32(epi, a, nreal, nr, ds, st);
-        case HISQ_F16: return dslash_launch_HISQ_F16_HISQ_F16(epi, a, nreal, nr, ds, st);
-        case HISQ_BF16: return dslash_launch_HISQ_BF16_HISQ_BF16(epi, a, nreal, nr, ds, st);
+        case HISQ_F64: return dslash_launch_HISQ_F64_HISQ_F64(epi, b, nreal, nr, ds, st);
+        case HISQ_F64X: return dslash_launch_HISQ_F64X_HISQ_F64X(epi, b, nreal, nr, ds, st);
+        case HISQ_F32: return dslash_launch_HISQ_F32_HISQ_F32(epi, b, nreal, nr, ds, st);
+        case HISQ_F16: return dslash_launch_HISQ_F16_HISQ_F16(epi, b, nreal, nr, ds, st);
+        case HISQ_BF16: return dslash_launch_HISQ_BF16_HISQ_BF16(epi, b, nreal, nr, ds, st);
         }
     } else if (pv == HISQ_F32) {
-        if (pl == HISQ_F16) return dslash_launch_HISQ_F16_HISQ_F32(epi, a, nreal, nr, ds, st);
-        if (pl == HISQ_BF16) return dslash_launch_HISQ_BF16_HISQ_F32(epi, a, nreal, nr, ds, st);
+        if (pl == HISQ_F16) return dslash_launch_HISQ_F16_HISQ_F32(epi, b, nreal, nr, ds, st);
+        if (pl == HISQ_BF16) return dslash_launch_HISQ_BF16_HISQ_F32(epi, b, nreal, nr, ds, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -51,7 +53,16 @@ DslashArgs make_dslash_args(hisq_ctx *ctx, int prec, int out_parity, const void 
     a.out = static_cast<char *>(out);
     a.rhs_bytes = rhs_bytes;
     a.nrhs = nrhs;
+    a.stream_links = L.slot_bytes * kSlots > ctx->l2_persist_max;
+    a.sm_count = ctx->sm_count;
     return a;
+}
+
+// z-t interchanged launch order by default when several right-hand sides share the links
+// and their spinors do not fit in L2 together
+static int default_order(hisq_ctx *ctx, int pv, int nrhs)
+{
+    return ctx->g.zt_ok && nrhs > 1 && (size_t)nrhs * ctx->g.VhPad * spinor_bytes(pv) > (64u << 20) ? 1 : 0;
 }
 
 static DslashShape default_shape(hisq_ctx *ctx, int pv, int nrhs)
@@ -59,13 +70,15 @@ static DslashShape default_shape(hisq_ctx *ctx, int pv, int nrhs)
     DslashShape s;
     s.nr = pick_inner(pv, nrhs);
     s.ds = ctx->g.Vh < (1u << 20) ? 2 : 1;
+    s.order = default_order(ctx, pv, nrhs);
     return s;
 }
 
-// Autotuner: every (N_inner, threads-per-site) shape that divides the work is timed on the
-// caller's buffers (best of two rounds of 3 launches after one warm-up, CUDA events on the
-// caller's stream) the first time a key is seen; a shape replaces the size-based default
-// only when it is at least 3% faster.  The choice is kept for the context's lifetime.
+// Autotuner: every (N_inner, threads-per-site, site order) shape that divides the work is
+// timed on the caller's buffers (best of two rounds of 3 launches after one warm-up, CUDA
+// events on the caller's stream) the first time a key is seen; a shape replaces the
+// size-based default only when it is at least 3% faster.  The choice is kept for the
+// context's lifetime.
 DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in, void *out, size_t rhs_bytes,
                          cudaStream_t st)
 {
@@ -109,18 +122,19 @@ DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in
     };
     const DslashShape def = best;
     float best_ms = time_shape(def);
-    for (int nr = 1; nr <= cap; nr <<= 1) {
-        if (nrhs % nr) continue;
-        for (int ds = 1; ds <= 4; ds <<= 1) {
-            DslashShape sh{nr, ds};
-            if (sh.nr == def.nr && sh.ds == def.ds) continue;
-            const float ms = time_shape(sh);
-            if (ms < 0.97f * best_ms) {
-                best_ms = ms;
-                best = sh;
+    for (int order = 0; order <= (ctx->g.zt_ok ? 1 : 0); order++)
+        for (int nr = 1; nr <= cap; nr <<= 1) {
+            if (nrhs % nr) continue;
+            for (int ds = 1; ds <= 4; ds <<= 1) {
+                DslashShape sh{nr, ds, order};
+                if (sh.nr == def.nr && sh.ds == def.ds && sh.order == def.order) continue;
+                const float ms = time_shape(sh);
+                if (ms < 0.97f * best_ms) {
+                    best_ms = ms;
+                    best = sh;
+                }
             }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->tune[key] = best;
@@ -149,7 +163,7 @@ int launch_dslash(hisq_ctx *ctx, int prec, int out_parity, const void *in, void 
 using namespace hisq;
 
 extern "C" int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int n_inner,
-                             int threads_per_site)
+                             int threads_per_site, int site_order)
 {
     if (!ctx) return HISQ_EINVAL;
     const bool pair_ok = prec_links >= 0 && prec_links < HISQ_NPREC &&
@@ -157,9 +171,11 @@ extern "C" int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, in
                                                                                        prec_links == HISQ_BF16)));
     const int cap = (prec_vectors == HISQ_F64 || prec_vectors == HISQ_F64X) ? 4 : 8;
     if (!pair_ok || nrhs < 1 || nrhs > 255 || (n_inner != 1 && n_inner != 2 && n_inner != 4 && n_inner != 8) ||
-        n_inner > cap || nrhs % n_inner || (threads_per_site != 1 && threads_per_site != 2 && threads_per_site != 4))
+        n_inner > cap || nrhs % n_inner || (threads_per_site != 1 && threads_per_site != 2 && threads_per_site != 4) ||
+        site_order < -1 || site_order > 1 || (site_order == 1 && !ctx->g.zt_ok))
         return set_error(ctx, HISQ_EINVAL, "hisq_tune_set: bad shape");
-    ctx->tune[(prec_links * 8 + prec_vectors) * 256 + nrhs] = DslashShape{n_inner, threads_per_site};
+    const int order = site_order >= 0 ? site_order : default_order(ctx, prec_vectors, nrhs);
+    ctx->tune[(prec_links * 8 + prec_vectors) * 256 + nrhs] = DslashShape{n_inner, threads_per_site, order};
     return HISQ_OK;
 }
 

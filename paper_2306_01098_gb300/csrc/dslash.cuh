@@ -24,6 +24,10 @@ struct DslashArgs {
     double m4;
     const double *shift;   // optional per right-hand side addition to m4 (device)
     Reduce red;
+    int zt;                // launch order with z and t interchanged (Geom::zt_ok required)
+    int stream_links;      // link store larger than L2 can keep: load links evict-first
+    int sm_count;          // SMs of the device (grid size)
+    uint32_t items;        // work items of the launch (set by the launcher)
 };
 
 DslashArgs make_dslash_args(hisq_ctx *ctx, int prec, int out_parity, const void *in, void *out, int nrhs,
@@ -31,6 +35,8 @@ DslashArgs make_dslash_args(hisq_ctx *ctx, int prec, int out_parity, const void 
 // pl: link storage precision, pv: vector precision (equal, or 16-bit links with FP32 vectors)
 cudaError_t dslash_launch(int pl, int pv, int epi, const DslashArgs &a, int nreal, const DslashShape &sh,
                           cudaStream_t st);
+// The launcher fills red.nblocks (partials per right-hand side, at most the site tiles of
+// the launch) and red.ntotal (blocks) of an epilogue reduction.
 // shape for (pl, pv, nrhs) on this context: measured once per key (autotuner) unless tuning
 // is off or the stream is capturing, then a size-based default
 DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in, void *out, size_t rhs_bytes,

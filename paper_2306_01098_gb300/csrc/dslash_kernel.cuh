@@ -8,8 +8,16 @@
 //
 // Work decomposition
 //   * NR right-hand sides per thread (the paper's N_inner loop, Sec. 5.1): every link is
-//     loaded once per NR vectors; grid.y runs over groups of NR right-hand sides (N_outer),
-//     adjacent in launch order so the next group finds the links in L2.
+//     loaded once per NR vectors.  The groups of NR right-hand sides (N_outer) are the
+//     fastest index of the block number, so the blocks that read one tile of links run
+//     together and only the first takes the links from HBM.
+//   * Launch order of the sites: storage order, or with z and t interchanged (t runs
+//     fastest among the planes).  A site's +-1/+-3 neighbours along the slowest launch
+//     dimension were touched 1 to 3 slowest-dimension slices earlier; interchanging z and
+//     t when Nt < Nz shrinks that reuse distance, and with it the L2 footprint that keeps
+//     neighbour spinors of many right-hand sides resident.  Link stores too large for L2
+//     are then read with an evict-first policy so that the streamed links do not displace
+//     the spinors.
 //   * DS threads per site (1, 2 or 4), each taking 4/DS of the directions; the partial sums
 //     meet through warp shuffles.  On small lattices one thread per site leaves a single
 //     short wave whose duration is the latency of 16 dependent gathers; splitting the
@@ -20,6 +28,8 @@
 // Optional epilogue (normal operator, Sec. 3.2 applyMdaggM):
 //   out = m4 * p - D in,   and <p, out> reduced in FP64 per right-hand side.
 #pragma once
+
+#include <algorithm>
 
 #include "arith.cuh"
 #include "dslash.cuh"
@@ -42,121 +52,160 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
         for (int r = 0; r < a.nrhs; r++) any |= a.skip[r].active != 0;
         if (!any) return;
     }
-    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t s = gt / DS;
-    const int part = (int)(gt % DS);
-    const int rhs0 = blockIdx.y * NR;
-    const bool live = s < a.g.Vh;
+    // gridDim.x is a multiple of the group count, so a block keeps one group of right-hand
+    // sides while it strides over the work items (site tile, group)
+    const uint32_t ngroups = (uint32_t)(a.nrhs / NR);
+    const int rhs0 = (int)(blockIdx.x % ngroups) * NR;
     double dots[NR];
 #pragma unroll
     for (int r = 0; r < NR; r++) dots[r] = 0.0;
 
-    typename T::Acc out[NR];
+    for (uint32_t item = blockIdx.x; item < a.items; item += gridDim.x) {
+        const uint32_t tile = item / ngroups;
+        const uint32_t gt = tile * kDslashBlock + threadIdx.x;
+        const uint32_t u = gt / DS; // site number in launch order
+        const int part = (int)(gt % DS);
+        const bool live = u < a.g.Vh;
+        uint32_t s = u;
+        if (a.zt) { // u = ((z Nt + t) Ps + i)  ->  s = ((t Nz + z) Ps + i), Ps = sites of one plane
+            const uint32_t plane = a.g.dp.div(u);
+            const uint32_t z = a.g.dt.div(plane);
+            s = ((plane - z * (uint32_t)a.g.n[3]) * (uint32_t)a.g.n[2] + z) * a.g.sz + (u - plane * a.g.sz);
+        }
+        typename T::Acc out[NR];
 #pragma unroll
-    for (int r = 0; r < NR; r++) T::zero(out[r]);
+        for (int r = 0; r < NR; r++) T::zero(out[r]);
 
-    if (live) {
-        const Site c = site_coords(a.g, s, a.p);
-        typename T::Acc acc[TWO ? 2 : 1][NR];
+        if (live) {
+            const Site c = site_coords(a.g, s, a.p);
+            typename T::Acc acc[TWO ? 2 : 1][NR];
 #pragma unroll
-        for (int t = 0; t < (TWO ? 2 : 1); t++)
+            for (int t = 0; t < (TWO ? 2 : 1); t++)
 #pragma unroll
-            for (int r = 0; r < NR; r++) T::zero(acc[t][r]);
+                for (int r = 0; r < NR; r++) T::zero(acc[t][r]);
 
 #pragma unroll
-        for (int m = 0; m < NMU; m++) {
-            const int mu = part * NMU + m;
-            typename T::Acc dacc[SPLIT ? NR : 1];
-            if constexpr (SPLIT) {
+            for (int m = 0; m < NMU; m++) {
+                const int mu = part * NMU + m;
+                typename T::Acc dacc[SPLIT ? NR : 1];
+                if constexpr (SPLIT) {
 #pragma unroll
-                for (int r = 0; r < NR; r++) T::zero(dacc[r]);
-            }
+                    for (int r = 0; r < NR; r++) T::zero(dacc[r]);
+                }
 #pragma unroll
-            for (int h = 0; h < 4; h++) {
-                const int k = h == 0 ? 1 : h == 1 ? -1 : h == 2 ? 3 : -3;
-                const int type = h >> 1;
-                const bool back = h & 1;
-                bool wrap;
-                const uint32_t sn = neighbour(a.g, c, s, mu, k, wrap);
-                const int lp = back ? 1 - a.p : a.p;
-                const char *slot = a.links + (size_t)((lp * 2 + type) * 4 + mu) * a.slot_bytes;
-                uint32_t w[LB / 4];
-                load_link_words<LB>(slot, back ? sn : s, w);
-                typename T::Link U;
-                TL::template unpack<NREAL>(w, U);
-                if constexpr (NREAL == 12) T::rebuild(U, (eta_neg(c, mu) != 0) ^ (mu == 3 && wrap));
+                for (int h = 0; h < 4; h++) {
+                    const int k = h == 0 ? 1 : h == 1 ? -1 : h == 2 ? 3 : -3;
+                    const int type = h >> 1;
+                    const bool back = h & 1;
+                    bool wrap;
+                    const uint32_t sn = neighbour(a.g, c, s, mu, k, wrap);
+                    const int lp = back ? 1 - a.p : a.p;
+                    const char *slot = a.links + (size_t)((lp * 2 + type) * 4 + mu) * a.slot_bytes;
+                    uint32_t w[LB / 4];
+                    load_link_words<LB>(slot, back ? sn : s, w, NR > 1 && a.stream_links != 0);
+                    typename T::Link U;
+                    TL::template unpack<NREAL>(w, U);
+                    if constexpr (NREAL == 12) T::rebuild(U, (eta_neg(c, mu) != 0) ^ (mu == 3 && wrap));
 #pragma unroll
-                for (int r = 0; r < NR; r++) {
-                    typename T::Vec v;
-                    T::load(a.in + (size_t)(rhs0 + r) * a.rhs_bytes, sn, v);
-                    typename T::Acc &dst = SPLIT ? dacc[SPLIT ? r : 0] : acc[TWO ? type : 0][r];
-                    if (back) T::template hop<true, true>(dst, U, v);
-                    else T::template hop<false, false>(dst, U, v);
+                    for (int r = 0; r < NR; r++) {
+                        typename T::Vec v;
+                        T::load(a.in + (size_t)(rhs0 + r) * a.rhs_bytes, sn, v);
+                        typename T::Acc &dst = SPLIT ? dacc[SPLIT ? r : 0] : acc[TWO ? type : 0][r];
+                        if (back) T::template hop<true, true>(dst, U, v);
+                        else T::template hop<false, false>(dst, U, v);
+                    }
+                }
+                if constexpr (SPLIT) {
+#pragma unroll
+                    for (int r = 0; r < NR; r++) {
+                        if (m == 0) acc[0][r] = dacc[r];
+                        else T::add_acc(acc[0][r], dacc[r]);
+                    }
                 }
             }
-            if constexpr (SPLIT) {
 #pragma unroll
-                for (int r = 0; r < NR; r++) {
-                    if (m == 0) acc[0][r] = dacc[r];
-                    else T::add_acc(acc[0][r], dacc[r]);
+            for (int r = 0; r < NR; r++) {
+                if constexpr (TWO) {
+                    T::axpy_acc(out[r], (typename T::Real)a.scale[0], acc[0][r]);
+                    T::axpy_acc(out[r], (typename T::Real)a.scale[1], acc[1][r]);
+                } else {
+                    out[r] = acc[0][r];
                 }
             }
         }
+        // partial sums of the DS threads of a site meet in every one of them
+        if constexpr (DS > 1) {
 #pragma unroll
-        for (int r = 0; r < NR; r++) {
-            if constexpr (TWO) {
-                T::axpy_acc(out[r], (typename T::Real)a.scale[0], acc[0][r]);
-                T::axpy_acc(out[r], (typename T::Real)a.scale[1], acc[1][r]);
-            } else {
-                out[r] = acc[0][r];
-            }
+            for (int off = DS / 2; off > 0; off >>= 1)
+#pragma unroll
+                for (int r = 0; r < NR; r++) T::shfl_xor_add(out[r], off);
         }
-    }
-    // partial sums of the DS threads of a site meet in every one of them
-    if constexpr (DS > 1) {
+        if (live && part == 0) {
 #pragma unroll
-        for (int off = DS / 2; off > 0; off >>= 1)
-#pragma unroll
-            for (int r = 0; r < NR; r++) T::shfl_xor_add(out[r], off);
-    }
-    if (live && part == 0) {
-#pragma unroll
-        for (int r = 0; r < NR; r++) {
-            if constexpr (EPI == 1) {
-                typename T::Vec pv;
-                T::load(a.pv + (size_t)(rhs0 + r) * a.rhs_bytes, s, pv);
-                T::mdagm_epilogue(out[r], a.shift ? a.m4 + a.shift[rhs0 + r] : a.m4, pv);
-                dots[r] = T::dot(pv, out[r]);
+            for (int r = 0; r < NR; r++) {
+                if constexpr (EPI == 1) {
+                    typename T::Vec pv;
+                    T::load(a.pv + (size_t)(rhs0 + r) * a.rhs_bytes, s, pv);
+                    T::mdagm_epilogue(out[r], a.shift ? a.m4 + a.shift[rhs0 + r] : a.m4, pv);
+                    dots[r] += T::dot(pv, out[r]);
+                }
+                T::store(a.out + (size_t)(rhs0 + r) * a.rhs_bytes, s, out[r]);
             }
-            T::store(a.out + (size_t)(rhs0 + r) * a.rhs_bytes, s, out[r]);
         }
     }
     if constexpr (EPI == 1) {
         if (a.red.partials) { // uniform over the grid
-            double mine[NR];
-#pragma unroll
-            for (int r = 0; r < NR; r++) mine[r] = block_sum(dots[r]);
-            grid_reduce<NR>(a.red, mine, NR, rhs0, a.nrhs, blockIdx.x);
+            block_sum_multi<NR>(dots);
+            grid_reduce<NR>(a.red, dots, NR, rhs0, a.nrhs, (int)(blockIdx.x / ngroups));
         }
     }
 }
 
 // ---------------------------------------------------------------- launch table
+// Work items are (site tile of kDslashBlock threads, group of NR right-hand sides), the
+// group fastest.  Without a reduction every item is a block of its own.  With the
+// epilogue's reduction the grid holds at most as many blocks as are resident at once (a
+// multiple of the group count, from the occupancy of this instantiation) and blocks
+// stride over the items, so that there is one partial per block and right-hand side.
+template <int PL, int PV, int NREAL, int NR, int EPI, int DS>
+static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
+{
+    static int occ = -1; // resident blocks per SM of this instantiation
+    if (occ < 0) {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_dslash<PL, PV, NREAL, NR, EPI, DS>, kDslashBlock, 0) !=
+                cudaSuccess || o < 1)
+            o = 1;
+        occ = o;
+    }
+    DslashArgs a = a0;
+    const size_t tiles = ((size_t)a.g.Vh * DS + kDslashBlock - 1) / kDslashBlock;
+    const size_t ng = (size_t)(a.nrhs / NR);
+    const size_t items = tiles * ng;
+    const size_t resident = std::max<size_t>(ng, (size_t)std::max(1, a.sm_count) * occ / ng * ng);
+    const size_t blocks = a.red.partials ? std::min(items, resident) : items;
+    if (items > 0xffffffffull) return cudaErrorInvalidValue;
+    a.items = (uint32_t)items;
+    a.red.nblocks = (int)(blocks / ng); // partials per right-hand side
+    a.red.ntotal = (int)blocks;
+    k_dslash<PL, PV, NREAL, NR, EPI, DS><<<(unsigned)blocks, kDslashBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int PL, int PV, int NREAL, int EPI, int DS>
 static cudaError_t launch_nr(const DslashArgs &a, int nr, cudaStream_t st)
 {
-    dim3 grid((unsigned)(((size_t)a.g.Vh * DS + kDslashBlock - 1) / kDslashBlock), a.nrhs / nr);
+    if (a.zt && !a.g.zt_ok) return cudaErrorInvalidValue;
+    if (a.nrhs < 1 || a.nrhs % nr) return cudaErrorInvalidValue;
     switch (nr) {
-    case 1: k_dslash<PL, PV, NREAL, 1, EPI, DS><<<grid, kDslashBlock, 0, st>>>(a); break;
-    case 2: k_dslash<PL, PV, NREAL, 2, EPI, DS><<<grid, kDslashBlock, 0, st>>>(a); break;
-    case 4: k_dslash<PL, PV, NREAL, 4, EPI, DS><<<grid, kDslashBlock, 0, st>>>(a); break;
+    case 1: return launch_one<PL, PV, NREAL, 1, EPI, DS>(a, st);
+    case 2: return launch_one<PL, PV, NREAL, 2, EPI, DS>(a, st);
+    case 4: return launch_one<PL, PV, NREAL, 4, EPI, DS>(a, st);
     case 8:
         if constexpr (PV == HISQ_F64 || PV == HISQ_F64X) return cudaErrorInvalidValue;
-        else k_dslash<PL, PV, NREAL, 8, EPI, DS><<<grid, kDslashBlock, 0, st>>>(a);
-        break;
+        else return launch_one<PL, PV, NREAL, 8, EPI, DS>(a, st);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <int PL, int PV, int NREAL, int EPI>

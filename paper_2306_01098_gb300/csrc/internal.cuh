@@ -56,6 +56,8 @@ struct Geom {
     uint32_t VhPad;     // Vh rounded up to a multiple of 128
     uint32_t sy, sz, st;// half-index strides of y, z, t: nxh, nxh Ny, nxh Ny Nz
     FastDiv dx, dy, dz; // divide by nxh, Ny, Nz
+    FastDiv dp, dt;     // divide by nxh Ny (sites of one z-t plane), Nt
+    int zt_ok;          // the z-t interchanged site order is available (planes of whole warps, Nt < Nz)
 };
 
 struct Site {
@@ -190,6 +192,7 @@ struct MsWork;
 struct DslashShape {
     int nr = 1;
     int ds = 1;
+    int order = 0; // 0: sites in storage order (t slowest); 1: z and t interchanged in launch order
 };
 
 }  // namespace hisq
@@ -198,6 +201,7 @@ struct DslashShape {
 struct hisq_ctx {
     int device = 0;
     int sm_count = 0;
+    size_t l2_persist_max = 0; // largest persisting L2 carve-out (bytes)
     int dims[4] = {0, 0, 0, 0};
     hisq::Geom g{};
     int links_phased = 0;

@@ -283,8 +283,7 @@ static int ms_iteration(hisq_ctx *ctx, MsWork &w, double m4s, cudaStream_t st)
     b.skip = w.sc;
     b.pv = w.p;
     b.m4 = m4s;
-    const int gx = (int)(((size_t)w.Vh * w.shape.ds + kDslashBlock - 1) / kDslashBlock); // blocks of this launch
-    b.red = w.red(FIN_ALPHA, gx, gx);
+    b.red = w.red(FIN_ALPHA, 0, 0); // block counts filled in by the launcher
     e = dslash_launch(w.ps, w.pv, 1, b, L.nreal, w.shape, st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "multishift dslash + epilogue");
     ms_dispatch(w.pv, [&](auto T) { decltype(T)::update_r(w, st); });

@@ -133,6 +133,45 @@ __device__ __forceinline__ double block_sum(double x)
     return r;
 }
 
+// loop control after the final sums (thread 0)
+__device__ __forceinline__ void finish_control(const Reduce &R, int nval_all)
+{
+    if (R.ctl) {
+        bool any = false;
+        for (int v = 0; v < nval_all; v++) any |= R.sc[v].active != 0;
+        const bool last = R.sc[0].it_all - R.ctl->start >= R.ctl->cap;
+        R.ctl->mode = last ? 1 : 0;
+        if (R.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)R.cond, (any && !last) ? 1u : 0u);
+    }
+}
+
+// block-wide sums of NV doubles at once (one barrier for all); results valid on thread 0
+template <int NV>
+__device__ __forceinline__ void block_sum_multi(double (&x)[NV])
+{
+    __shared__ double wsum[NV][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int v = 0; v < NV; v++) x[v] += __shfl_down_sync(0xffffffffu, x[v], o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0)
+#pragma unroll
+        for (int v = 0; v < NV; v++) wsum[v][w] = x[v];
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            double r = l < nw ? wsum[v][l] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+            x[v] = r;
+        }
+    }
+}
+
 // Grid reduction of `nval_all` values.  Block (bx, by) supplies the block sums of values
 // [vbase, vbase + nmine) (thread 0 holds them in `mine`) as partial number bx of each;
 // the last of the R.ntotal blocks to arrive sums the R.nblocks partials of every value
@@ -152,20 +191,19 @@ __device__ __forceinline__ void grid_reduce(const Reduce &R, const double (&mine
     if (!last) return;
     __threadfence();
     for (int v = 0; v < nval_all; v++) {
+        const double *pv = R.partials + (size_t)v * R.nblocks;
         double x = 0.0;
-        for (int i = threadIdx.x; i < R.nblocks; i += blockDim.x)
-            x += __ldcg(R.partials + (size_t)v * R.nblocks + i);
+        for (int i0 = threadIdx.x; i0 < R.nblocks; i0 += 4 * blockDim.x) {
+            double t[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) t[u] = i0 + u * (int)blockDim.x < R.nblocks ? __ldcg(pv + i0 + u * blockDim.x) : 0.0;
+            x += (t[0] + t[1]) + (t[2] + t[3]);
+        }
         x = block_sum(x);
         if (threadIdx.x == 0) finish_value(R, v, x);
     }
     if (threadIdx.x == 0) {
-        if (R.ctl) {
-            bool any = false;
-            for (int v = 0; v < nval_all; v++) any |= R.sc[v].active != 0;
-            const bool last = R.sc[0].it_all - R.ctl->start >= R.ctl->cap;
-            R.ctl->mode = last ? 1 : 0;
-            if (R.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)R.cond, (any && !last) ? 1u : 0u);
-        }
+        finish_control(R, nval_all);
         __threadfence();
         *R.counter = 0u;
     }

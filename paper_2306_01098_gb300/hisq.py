@@ -80,7 +80,7 @@ _SIGS = {
     "hisq_dslash_field": (_I, [_P, _I, _P, _P, _P]),
     "hisq_mdagm": (_I, [_P, _D, _P, _P, _I, _I, _P]),
     "hisq_mdagm_noalloc": (_I, [_P, _D, _P, _P, _I, _P]),
-    "hisq_tune_set": (_I, [_P, _I, _I, _I, _I, _I]),
+    "hisq_tune_set": (_I, [_P, _I, _I, _I, _I, _I, _I]),
     "hisq_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "hisq_cg": (_I, [_P, _D, _P, _P, _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
     "hisq_multishift_cg": (_I, [_P, _D, _I, _P, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
@@ -188,8 +188,9 @@ class Context:
         nrhs = inp.numel() // (self.Vh * 3)
         return self.check(lib().hisq_mdagm_noalloc(self.h, float(m), _ptr(inp), _ptr(out), nrhs, _stream(stream)))
 
-    def tune_set(self, prec_links, prec_vectors, nrhs, n_inner, threads_per_site):
-        return self.check(lib().hisq_tune_set(self.h, prec_links, prec_vectors, nrhs, n_inner, threads_per_site))
+    def tune_set(self, prec_links, prec_vectors, nrhs, n_inner, threads_per_site, site_order=-1):
+        return self.check(lib().hisq_tune_set(self.h, prec_links, prec_vectors, nrhs, n_inner, threads_per_site,
+                                              site_order))
 
     def field(self, prec, nrhs=1):
         return Field(self, prec, nrhs)

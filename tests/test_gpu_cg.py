@@ -117,7 +117,8 @@ def test_profiled_solve_counts_dslash_launches():
     x = torch.zeros_like(b)
     rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, profile=1, check_interval=10)
     assert rc == hisq.OK
-    # the two Dslash launches of the first iteration of every phase are timed
+    # the two Dslash launches of the second iteration of every phase of three or more
+    # iterations are timed
     assert st.dslash_timed % 2 == 0 and 2 <= st.dslash_timed <= 2 * st.iterations and st.dslash_ms > 0
 
 
@@ -144,3 +145,48 @@ def test_zero_source_returns_zero():
     x = torch.ones_like(b)
     rc, st = ctx.cg(m, b, x, tol=1e-10)
     assert x.abs().max().item() == 0.0 and st.iterations == 0
+
+
+@pytest.mark.parametrize("sloppy,nrhs", [(hisq.F64, 2), (hisq.F32, 4), (hisq.F16, 8)])
+def test_cg_z_t_interchanged_order(sloppy, nrhs):
+    # the solver's Dslash pair (with the fused epilogue and its reduction) in the z-t
+    # interchanged launch order gives the same solutions within tol
+    dims, m = (8, 8, 6, 4), 0.05
+    ctx, fat, lng = setup(dims, 0.5, 1030)
+    pv = hisq.F32 if sloppy == hisq.F16 else sloppy
+    b = fields.gaussian_source(dims, 2300, nrhs)
+    its = []
+    for order in (0, 1):
+        ctx.tune_set(sloppy, pv, nrhs, 2 if nrhs % 2 == 0 else 1, 2, order)
+        x = torch.zeros_like(b).cuda()
+        res = torch.zeros(nrhs, dtype=torch.float64)
+        rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=sloppy, prec_precise=hisq.F64, residuals=res)
+        assert rc == hisq.OK
+        xg = x.cpu().numpy()
+        for r in range(nrhs):
+            assert true_res(dims, fat, lng, m, b[r].numpy(), xg[r]) <= 1e-10
+        its.append(st.iterations)
+    assert abs(its[0] - its[1]) <= 3, its
+    _cache.clear()
+
+
+@pytest.mark.parametrize("ds", [1, 4])
+def test_cg_many_reduction_chunks(ds):
+    # 32 x 32 x 16 x 16 with 8 right-hand sides: 1024 (ds 1) or 4096 (ds 4) blocks per
+    # right-hand side and Dslash launch, so the epilogue's reduction runs single-level
+    # (8192 partials) or in two levels over 32 chunks of 128 (32768 partials)
+    dims, m, nrhs = (32, 32, 16, 16), 0.1, 8
+    fat_d, lng_d = fields.recipe_links(dims, 0.3, 1040, device="cuda")
+    ctx = hisq.Context(dims, fat_d, lng_d, precs=(hisq.F64, hisq.F32))
+    fat, lng = fat_d.cpu().numpy(), lng_d.cpu().numpy()
+    del fat_d, lng_d
+    b = fields.gaussian_source(dims, 2400, nrhs)
+    ctx.tune_set(hisq.F32, hisq.F32, nrhs, 2, ds, -1)
+    x = torch.zeros_like(b).cuda()
+    res = torch.zeros(nrhs, dtype=torch.float64)
+    rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, residuals=res)
+    assert rc == hisq.OK
+    xg = x.cpu().numpy()
+    for r in range(nrhs):
+        assert true_res(dims, fat, lng, m, b[r].numpy(), xg[r]) <= 1e-10
+    ctx.close()

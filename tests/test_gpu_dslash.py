@@ -244,3 +244,42 @@ def test_argument_errors():
         with pytest.raises(hisq.HisqError):
             hisq.Context(bad, torch.zeros(4, int(np.prod(bad)), 3, 3, dtype=torch.complex128).cuda(),
                          torch.zeros(4, int(np.prod(bad)), 3, 3, dtype=torch.complex128).cuda())
+
+
+@pytest.mark.parametrize("prec", [hisq.F64, hisq.F32, hisq.F16])
+def test_dslash_site_orders(prec):
+    # 8 x 8 x 6 x 4: one z-t plane holds 32 sites and Nt < Nz, so the z-t interchanged
+    # launch order is available; both orders, every shape, both parities give the operator
+    dims, nrhs = (8, 8, 6, 4), 8
+    ctx, fat, lng = setup(dims)
+    pv = hisq.F32 if prec == hisq.F16 else prec
+    tol = {hisq.F32: 2e-6, hisq.F16: 3e-3}.get(prec)
+    for p in (0, 1):
+        x = fields.gaussian_source(dims, 190 + p, nrhs)
+        want = oracle.dslash(dims, fat, lng, x, p)
+        for order in (0, 1):
+            for nr in (1, 4, 8):
+                if nr == 8 and prec == hisq.F64:
+                    continue
+                for ds in (1, 4):
+                    ctx.tune_set(prec, pv, nrhs, nr, ds, order)
+                    out = torch.full_like(x, float("nan")).cuda()
+                    ctx.dslash(p, x.cuda(), out, prec=prec)
+                    got = out.cpu().numpy()
+                    for r in range(nrhs):
+                        if tol is None:
+                            assert site_rel(got[r], want[r]) <= 1e-13, (order, nr, ds, r)
+                        else:
+                            assert field_rel(got[r], want[r]) <= tol, (order, nr, ds, r)
+    _cache.clear()
+
+
+def test_site_order_rejected_where_unavailable():
+    dims = (6, 4, 4, 8)  # a z-t plane of 12 sites: only storage order
+    ctx, fat, lng = setup(dims)
+    with pytest.raises(hisq.HisqError):
+        ctx.tune_set(hisq.F64, hisq.F64, 1, 1, 1, 1)
+    with pytest.raises(hisq.HisqError):
+        ctx.tune_set(hisq.F64, hisq.F64, 1, 1, 1, 2)
+    ctx.tune_set(hisq.F64, hisq.F64, 1, 1, 1, 0)
+    _cache.clear()
