@@ -221,6 +221,37 @@ int hisq_multishift_cg(hisq_ctx *ctx, double m, int nshift, const double *sigma,
                        const double *b, double *const *x, const double *tol,
                        const hisq_solve_opts *opts, hisq_stats *stats, double *residuals);
 
+/* ------------------------------------------------------------------ batches of lattices */
+/* Several lattices of different sizes (each its own context, links and mass) in single
+ * launches.  The paper runs one lattice at a time and has no counterpart; the Dslash of a
+ * batch is the operator of Sec. 5.1 applied to every member at once, the batched solver
+ * is the CG of Sec. 3.2 (with the mixed-precision scheme of hisq_cg) run on every member
+ * with its own scalars, iterations of all members sharing each launch. */
+typedef struct hisq_batch hisq_batch;
+
+/* A batch of n (1..32) contexts on one device.  The batch borrows the contexts, which must
+ * outlive it and keep their link stores; a precision is available in the batch when every
+ * member built it with the same compression.  Returns HISQ_EINVAL for a bad list. */
+int hisq_batch_create(hisq_batch **batch, int n, hisq_ctx *const *ctxs);
+void hisq_batch_destroy(hisq_batch *batch);
+/* total sites of one parity over the members (the length of packed vectors, in sites) */
+long hisq_batch_sites(const hisq_batch *batch);
+const char *hisq_batch_last_error_message(hisq_batch *batch);
+
+/* out = D_{out_parity, 1-out_parity} in for every member, one Dslash launch (plus the
+ * conversion kernels of a reduced precision).  in/out: packed canonical complex128 device
+ * vectors, member k's [Vh_k][3] sites after those of members 0..k-1; no overlap.  Calls on
+ * one batch must be serialised by the caller (they share the batch's padded buffers). */
+int hisq_batch_dslash(hisq_batch *batch, int out_parity, const double *in, double *out, int prec, void *stream);
+
+/* Solves (4 m_k^2 - D_eo D_oe) x_k = b_k on every member k, as hisq_cg does for one
+ * lattice (opts->prec_sloppy, prec_precise, reliable updates, graph); m: n masses (host),
+ * b, x: packed canonical device vectors (as for hisq_batch_dslash; host_buffers is not
+ * accepted).  `residuals` (may be NULL) receives n true residuals; stats as hisq_cg, over
+ * all members.  Returns HISQ_ENOTCONVERGED if any member misses opts->tol. */
+int hisq_batch_cg(hisq_batch *batch, const double *m, const double *b, double *x, const hisq_solve_opts *opts,
+                  hisq_stats *stats, double *residuals);
+
 /* ------------------------------------------------------------------ learned preconditioner */
 /* Not in the paper.  A gauge-covariant parallel-transport network K (layers of complex
  * channel mixing over 17 taps: identity, the 8 one-hop and 8 three-hop transports of the

@@ -55,6 +55,15 @@ DslashArgs make_dslash_args(hisq_ctx *ctx, int prec, int out_parity, const void 
     a.nrhs = nrhs;
     a.stream_links = L.slot_bytes * kSlots > ctx->l2_persist_max;
     a.sm_count = ctx->sm_count;
+    if (ctx->batch) {
+        a.batch = ctx->batch;
+        a.batch_n = ctx->batch_host->n;
+        for (int d = 0; d < 3; d++) {
+            a.batch_tiles[d] = ctx->batch_host->tstart[d][a.batch_n];
+            a.batch_maxtiles[d] = ctx->batch_host->maxtiles[d];
+        }
+        a.stream_links = 0;
+    }
     return a;
 }
 
@@ -68,7 +77,7 @@ static int default_order(hisq_ctx *ctx, int pv, int nrhs)
 static DslashShape default_shape(hisq_ctx *ctx, int pv, int nrhs)
 {
     DslashShape s;
-    s.nr = pick_inner(pv, nrhs);
+    s.nr = ctx->batch ? 1 : pick_inner(pv, nrhs);
     s.ds = ctx->g.Vh < (1u << 20) ? 2 : 1;
     s.order = default_order(ctx, pv, nrhs);
     return s;

@@ -28,6 +28,11 @@ struct DslashArgs {
     int stream_links;      // link store larger than L2 can keep: load links evict-first
     int sm_count;          // SMs of the device (grid size)
     uint32_t items;        // work items of the launch (set by the launcher)
+    // batch of lattices (NULL for one lattice): device table, lattices, and from the host
+    // copy of the table the tiles of all lattices / of the largest, per threads per site
+    const BatchDesc *batch;
+    int batch_n;
+    uint32_t batch_tiles[3], batch_maxtiles[3];
 };
 
 DslashArgs make_dslash_args(hisq_ctx *ctx, int prec, int out_parity, const void *in, void *out, int nrhs,

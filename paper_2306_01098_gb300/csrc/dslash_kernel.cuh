@@ -27,6 +27,8 @@
 //     PL and PV differ only for 16-bit links with FP32 vectors.
 // Optional epilogue (normal operator, Sec. 3.2 applyMdaggM):
 //   out = m4 * p - D in,   and <p, out> reduced in FP64 per right-hand side.
+// Batches: one launch over the lattices of a batch, each with its own geometry and links
+// (one right-hand side per lattice); a block finds its lattice in the batch table.
 #pragma once
 
 #include <algorithm>
@@ -37,126 +39,168 @@
 
 namespace hisq {
 
+// One work item: the sites of one tile (kDslashBlock threads, DS per site) for the NR
+// right-hand sides whose vectors start at in/out/pv (consecutive right-hand sides
+// a.rhs_bytes apart); geometry g, link store `links`.  Epilogue dot products are added to
+// dots.
 template <int PL, int PV, int NREAL, int NR, int EPI, int DS>
-__global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
+__device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, const char *links, size_t slot_bytes,
+                                            double sc0, double sc1, const char *in, char *outp, const char *pvp,
+                                            const double *m4r, uint32_t tile, double (&dots)[NR])
 {
     using T = Prec<PV>;  // vectors and arithmetic
     using TL = Prec<PL>; // link storage
-    static_assert(std::is_same<typename T::Link, typename TL::Link>::value, "link and vector arithmetic must agree");
     constexpr int LB = NREAL == 18 ? LinkBytes<PL>::b18 : LinkBytes<PL>::b12;
     constexpr bool TWO = (PL == HISQ_F16 || PL == HISQ_BF16 || NREAL == 12);
     constexpr bool SPLIT = T::kSplitDirections;
     constexpr int NMU = 4 / DS;
+    const uint32_t gt = tile * kDslashBlock + threadIdx.x;
+    const uint32_t u = gt / DS; // site number in launch order
+    const int part = (int)(gt % DS);
+    const bool live = u < g.Vh;
+    uint32_t s = u;
+    if (a.zt) { // u = ((z Nt + t) Ps + i)  ->  s = ((t Nz + z) Ps + i), Ps = sites of one plane
+        const uint32_t plane = g.dp.div(u);
+        const uint32_t z = g.dt.div(plane);
+        s = ((plane - z * (uint32_t)g.n[3]) * (uint32_t)g.n[2] + z) * g.sz + (u - plane * g.sz);
+    }
+    typename T::Acc out[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) T::zero(out[r]);
+
+    if (live) {
+        const Site c = site_coords(g, s, a.p);
+        typename T::Acc acc[TWO ? 2 : 1][NR];
+#pragma unroll
+        for (int t = 0; t < (TWO ? 2 : 1); t++)
+#pragma unroll
+            for (int r = 0; r < NR; r++) T::zero(acc[t][r]);
+
+#pragma unroll
+        for (int m = 0; m < NMU; m++) {
+            const int mu = part * NMU + m;
+            typename T::Acc dacc[SPLIT ? NR : 1];
+            if constexpr (SPLIT) {
+#pragma unroll
+                for (int r = 0; r < NR; r++) T::zero(dacc[r]);
+            }
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                const int k = h == 0 ? 1 : h == 1 ? -1 : h == 2 ? 3 : -3;
+                const int type = h >> 1;
+                const bool back = h & 1;
+                bool wrap;
+                const uint32_t sn = neighbour(g, c, s, mu, k, wrap);
+                const int lp = back ? 1 - a.p : a.p;
+                const char *slot = links + (size_t)((lp * 2 + type) * 4 + mu) * slot_bytes;
+                uint32_t w[LB / 4];
+                load_link_words<LB>(slot, back ? sn : s, w, NR > 1 && a.stream_links != 0);
+                typename T::Link U;
+                TL::template unpack<NREAL>(w, U);
+                if constexpr (NREAL == 12) T::rebuild(U, (eta_neg(c, mu) != 0) ^ (mu == 3 && wrap));
+#pragma unroll
+                for (int r = 0; r < NR; r++) {
+                    typename T::Vec v;
+                    T::load(in + (size_t)r * a.rhs_bytes, sn, v);
+                    typename T::Acc &dst = SPLIT ? dacc[SPLIT ? r : 0] : acc[TWO ? type : 0][r];
+                    if (back) T::template hop<true, true>(dst, U, v);
+                    else T::template hop<false, false>(dst, U, v);
+                }
+            }
+            if constexpr (SPLIT) {
+#pragma unroll
+                for (int r = 0; r < NR; r++) {
+                    if (m == 0) acc[0][r] = dacc[r];
+                    else T::add_acc(acc[0][r], dacc[r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            if constexpr (TWO) {
+                T::axpy_acc(out[r], (typename T::Real)sc0, acc[0][r]);
+                T::axpy_acc(out[r], (typename T::Real)sc1, acc[1][r]);
+            } else {
+                out[r] = acc[0][r];
+            }
+        }
+    }
+    // partial sums of the DS threads of a site meet in every one of them
+    if constexpr (DS > 1) {
+#pragma unroll
+        for (int off = DS / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int r = 0; r < NR; r++) T::shfl_xor_add(out[r], off);
+    }
+    if (live && part == 0) {
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            if constexpr (EPI == 1) {
+                typename T::Vec pv;
+                T::load(pvp + (size_t)r * a.rhs_bytes, s, pv);
+                T::mdagm_epilogue(out[r], a.m4 + (m4r ? m4r[r] : 0.0), pv);
+                dots[r] += T::dot(pv, out[r]);
+            }
+            T::store(outp + (size_t)r * a.rhs_bytes, s, out[r]);
+        }
+    }
+}
+
+// BATCH: the lattices of a batch in one launch (NR = 1; right-hand side k is lattice k).
+template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH>
+__global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
+{
+    using T = Prec<PV>;
+    using TL = Prec<PL>;
+    static_assert(std::is_same<typename T::Link, typename TL::Link>::value, "link and vector arithmetic must agree");
+    static_assert(!BATCH || NR == 1, "batches take one right-hand side per lattice");
     if (a.skip) { // uniform over the grid: the scalars do not change during the launch
         bool any = false;
         for (int r = 0; r < a.nrhs; r++) any |= a.skip[r].active != 0;
         if (!any) return;
     }
-    // gridDim.x is a multiple of the group count, so a block keeps one group of right-hand
-    // sides while it strides over the work items (site tile, group)
-    const uint32_t ngroups = (uint32_t)(a.nrhs / NR);
-    const int rhs0 = (int)(blockIdx.x % ngroups) * NR;
     double dots[NR];
 #pragma unroll
     for (int r = 0; r < NR; r++) dots[r] = 0.0;
-
-    for (uint32_t item = blockIdx.x; item < a.items; item += gridDim.x) {
-        const uint32_t tile = item / ngroups;
-        const uint32_t gt = tile * kDslashBlock + threadIdx.x;
-        const uint32_t u = gt / DS; // site number in launch order
-        const int part = (int)(gt % DS);
-        const bool live = u < a.g.Vh;
-        uint32_t s = u;
-        if (a.zt) { // u = ((z Nt + t) Ps + i)  ->  s = ((t Nz + z) Ps + i), Ps = sites of one plane
-            const uint32_t plane = a.g.dp.div(u);
-            const uint32_t z = a.g.dt.div(plane);
-            s = ((plane - z * (uint32_t)a.g.n[3]) * (uint32_t)a.g.n[2] + z) * a.g.sz + (u - plane * a.g.sz);
-        }
-        typename T::Acc out[NR];
-#pragma unroll
-        for (int r = 0; r < NR; r++) T::zero(out[r]);
-
-        if (live) {
-            const Site c = site_coords(a.g, s, a.p);
-            typename T::Acc acc[TWO ? 2 : 1][NR];
-#pragma unroll
-            for (int t = 0; t < (TWO ? 2 : 1); t++)
-#pragma unroll
-                for (int r = 0; r < NR; r++) T::zero(acc[t][r]);
-
-#pragma unroll
-            for (int m = 0; m < NMU; m++) {
-                const int mu = part * NMU + m;
-                typename T::Acc dacc[SPLIT ? NR : 1];
-                if constexpr (SPLIT) {
-#pragma unroll
-                    for (int r = 0; r < NR; r++) T::zero(dacc[r]);
-                }
-#pragma unroll
-                for (int h = 0; h < 4; h++) {
-                    const int k = h == 0 ? 1 : h == 1 ? -1 : h == 2 ? 3 : -3;
-                    const int type = h >> 1;
-                    const bool back = h & 1;
-                    bool wrap;
-                    const uint32_t sn = neighbour(a.g, c, s, mu, k, wrap);
-                    const int lp = back ? 1 - a.p : a.p;
-                    const char *slot = a.links + (size_t)((lp * 2 + type) * 4 + mu) * a.slot_bytes;
-                    uint32_t w[LB / 4];
-                    load_link_words<LB>(slot, back ? sn : s, w, NR > 1 && a.stream_links != 0);
-                    typename T::Link U;
-                    TL::template unpack<NREAL>(w, U);
-                    if constexpr (NREAL == 12) T::rebuild(U, (eta_neg(c, mu) != 0) ^ (mu == 3 && wrap));
-#pragma unroll
-                    for (int r = 0; r < NR; r++) {
-                        typename T::Vec v;
-                        T::load(a.in + (size_t)(rhs0 + r) * a.rhs_bytes, sn, v);
-                        typename T::Acc &dst = SPLIT ? dacc[SPLIT ? r : 0] : acc[TWO ? type : 0][r];
-                        if (back) T::template hop<true, true>(dst, U, v);
-                        else T::template hop<false, false>(dst, U, v);
-                    }
-                }
-                if constexpr (SPLIT) {
-#pragma unroll
-                    for (int r = 0; r < NR; r++) {
-                        if (m == 0) acc[0][r] = dacc[r];
-                        else T::add_acc(acc[0][r], dacc[r]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < NR; r++) {
-                if constexpr (TWO) {
-                    T::axpy_acc(out[r], (typename T::Real)a.scale[0], acc[0][r]);
-                    T::axpy_acc(out[r], (typename T::Real)a.scale[1], acc[1][r]);
-                } else {
-                    out[r] = acc[0][r];
-                }
+    if constexpr (BATCH) {
+        __shared__ Geom sg;
+        constexpr int d = DS == 1 ? 0 : DS == 2 ? 1 : 2;
+        const BatchDesc &B = *a.batch;
+        const uint32_t item = blockIdx.x;
+        int k = 0;
+        while (k + 1 < B.n && B.tstart[d][k + 1] <= item) k++;
+        const uint32_t tile = item - B.tstart[d][k];
+        if (threadIdx.x == 0) sg = B.lat[k].g;
+        __syncthreads();
+        const size_t off = (size_t)k * a.rhs_bytes;
+        dslash_item<PL, PV, NREAL, 1, EPI, DS>(a, sg, B.lat[k].links[PL], B.lat[k].slot_bytes[PL], B.lat[k].scale[PL][0],
+                                               B.lat[k].scale[PL][1], a.in + off, a.out + off,
+                                               EPI ? a.pv + off : nullptr, a.shift ? a.shift + k : nullptr, tile, dots);
+        if constexpr (EPI == 1) {
+            if (a.red.partials) {
+                block_sum_multi<1>(dots);
+                // partials of lattice k beyond its own tiles are zero
+                if (threadIdx.x == 0 && tile == 0)
+                    for (int i = (int)(B.tstart[d][k + 1] - B.tstart[d][k]); i < a.red.nblocks; i++)
+                        a.red.partials[(size_t)k * a.red.nblocks + i] = 0.0;
+                grid_reduce<1>(a.red, dots, 1, k, a.nrhs, (int)tile);
             }
         }
-        // partial sums of the DS threads of a site meet in every one of them
-        if constexpr (DS > 1) {
-#pragma unroll
-            for (int off = DS / 2; off > 0; off >>= 1)
-#pragma unroll
-                for (int r = 0; r < NR; r++) T::shfl_xor_add(out[r], off);
-        }
-        if (live && part == 0) {
-#pragma unroll
-            for (int r = 0; r < NR; r++) {
-                if constexpr (EPI == 1) {
-                    typename T::Vec pv;
-                    T::load(a.pv + (size_t)(rhs0 + r) * a.rhs_bytes, s, pv);
-                    T::mdagm_epilogue(out[r], a.shift ? a.m4 + a.shift[rhs0 + r] : a.m4, pv);
-                    dots[r] += T::dot(pv, out[r]);
-                }
-                T::store(a.out + (size_t)(rhs0 + r) * a.rhs_bytes, s, out[r]);
+    } else {
+        // gridDim.x is a multiple of the group count, so a block keeps one group of right-hand
+        // sides while it strides over the work items (site tile, group)
+        const uint32_t ngroups = (uint32_t)(a.nrhs / NR);
+        const int rhs0 = (int)(blockIdx.x % ngroups) * NR;
+        const size_t off = (size_t)rhs0 * a.rhs_bytes;
+        for (uint32_t item = blockIdx.x; item < a.items; item += gridDim.x)
+            dslash_item<PL, PV, NREAL, NR, EPI, DS>(a, a.g, a.links, a.slot_bytes, a.scale[0], a.scale[1], a.in + off,
+                                                    a.out + off, EPI ? a.pv + off : nullptr,
+                                                    a.shift ? a.shift + rhs0 : nullptr, item / ngroups, dots);
+        if constexpr (EPI == 1) {
+            if (a.red.partials) { // uniform over the grid
+                block_sum_multi<NR>(dots);
+                grid_reduce<NR>(a.red, dots, NR, rhs0, a.nrhs, (int)(blockIdx.x / ngroups));
             }
-        }
-    }
-    if constexpr (EPI == 1) {
-        if (a.red.partials) { // uniform over the grid
-            block_sum_multi<NR>(dots);
-            grid_reduce<NR>(a.red, dots, NR, rhs0, a.nrhs, (int)(blockIdx.x / ngroups));
         }
     }
 }
@@ -167,43 +211,58 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
 // epilogue's reduction the grid holds at most as many blocks as are resident at once (a
 // multiple of the group count, from the occupancy of this instantiation) and blocks
 // stride over the items, so that there is one partial per block and right-hand side.
-template <int PL, int PV, int NREAL, int NR, int EPI, int DS>
+template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH>
 static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
 {
     static int occ = -1; // resident blocks per SM of this instantiation
     if (occ < 0) {
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_dslash<PL, PV, NREAL, NR, EPI, DS>, kDslashBlock, 0) !=
-                cudaSuccess || o < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_dslash<PL, PV, NREAL, NR, EPI, DS, BATCH>, kDslashBlock,
+                                                          0) != cudaSuccess ||
+            o < 1)
             o = 1;
         occ = o;
     }
     DslashArgs a = a0;
-    const size_t tiles = ((size_t)a.g.Vh * DS + kDslashBlock - 1) / kDslashBlock;
-    const size_t ng = (size_t)(a.nrhs / NR);
-    const size_t items = tiles * ng;
-    const size_t resident = std::max<size_t>(ng, (size_t)std::max(1, a.sm_count) * occ / ng * ng);
-    const size_t blocks = a.red.partials ? std::min(items, resident) : items;
-    if (items > 0xffffffffull) return cudaErrorInvalidValue;
-    a.items = (uint32_t)items;
-    a.red.nblocks = (int)(blocks / ng); // partials per right-hand side
-    a.red.ntotal = (int)blocks;
-    k_dslash<PL, PV, NREAL, NR, EPI, DS><<<(unsigned)blocks, kDslashBlock, 0, st>>>(a);
-    return cudaGetLastError();
+    if constexpr (BATCH) { // one block per tile of every lattice
+        constexpr int d = DS == 1 ? 0 : DS == 2 ? 1 : 2;
+        const uint32_t items = a.batch_tiles[d];
+        a.items = items;
+        a.red.nblocks = (int)a.batch_maxtiles[d]; // partials per lattice (zero beyond its tiles)
+        a.red.ntotal = (int)items;
+        k_dslash<PL, PV, NREAL, 1, EPI, DS, true><<<items, kDslashBlock, 0, st>>>(a);
+        return cudaGetLastError();
+    } else {
+        const size_t tiles = ((size_t)a.g.Vh * DS + kDslashBlock - 1) / kDslashBlock;
+        const size_t ng = (size_t)(a.nrhs / NR);
+        const size_t items = tiles * ng;
+        const size_t resident = std::max<size_t>(ng, (size_t)std::max(1, a.sm_count) * occ / ng * ng);
+        const size_t blocks = a.red.partials ? std::min(items, resident) : items;
+        if (items > 0xffffffffull) return cudaErrorInvalidValue;
+        a.items = (uint32_t)items;
+        a.red.nblocks = (int)(blocks / ng); // partials per right-hand side
+        a.red.ntotal = (int)blocks;
+        k_dslash<PL, PV, NREAL, NR, EPI, DS, false><<<(unsigned)blocks, kDslashBlock, 0, st>>>(a);
+        return cudaGetLastError();
+    }
 }
 
 template <int PL, int PV, int NREAL, int EPI, int DS>
 static cudaError_t launch_nr(const DslashArgs &a, int nr, cudaStream_t st)
 {
-    if (a.zt && !a.g.zt_ok) return cudaErrorInvalidValue;
     if (a.nrhs < 1 || a.nrhs % nr) return cudaErrorInvalidValue;
+    if (a.batch) { // one right-hand side per lattice, storage order
+        if (nr != 1 || a.zt || a.nrhs != a.batch_n) return cudaErrorInvalidValue;
+        return launch_one<PL, PV, NREAL, 1, EPI, DS, true>(a, st);
+    }
+    if (a.zt && !a.g.zt_ok) return cudaErrorInvalidValue;
     switch (nr) {
-    case 1: return launch_one<PL, PV, NREAL, 1, EPI, DS>(a, st);
-    case 2: return launch_one<PL, PV, NREAL, 2, EPI, DS>(a, st);
-    case 4: return launch_one<PL, PV, NREAL, 4, EPI, DS>(a, st);
+    case 1: return launch_one<PL, PV, NREAL, 1, EPI, DS, false>(a, st);
+    case 2: return launch_one<PL, PV, NREAL, 2, EPI, DS, false>(a, st);
+    case 4: return launch_one<PL, PV, NREAL, 4, EPI, DS, false>(a, st);
     case 8:
         if constexpr (PV == HISQ_F64 || PV == HISQ_F64X) return cudaErrorInvalidValue;
-        else return launch_one<PL, PV, NREAL, 8, EPI, DS>(a, st);
+        else return launch_one<PL, PV, NREAL, 8, EPI, DS, false>(a, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -195,6 +195,27 @@ struct DslashShape {
     int order = 0; // 0: sites in storage order (t slowest); 1: z and t interchanged in launch order
 };
 
+// ---------------------------------------------------------------- batches of lattices
+constexpr int kMaxBatch = 32;
+
+// one lattice of a batch: its geometry and the link stores of its context
+struct BatchLattice {
+    Geom g;
+    const char *links[HISQ_NPREC];
+    size_t slot_bytes[HISQ_NPREC];
+    double scale[HISQ_NPREC][2];
+};
+
+// Device table of a batch.  Work items of one launch are the site tiles of every lattice
+// in turn: lattice k owns items [tstart[d][k], tstart[d][k + 1]) at 2^d threads per site.
+// The vectors of lattice k start at right-hand side k of the padded solver layout.
+struct BatchDesc {
+    int n;
+    uint32_t tstart[3][kMaxBatch + 1];
+    uint32_t maxtiles[3]; // most tiles of one lattice
+    BatchLattice lat[kMaxBatch];
+};
+
 }  // namespace hisq
 
 // ---------------------------------------------------------------- context and fields
@@ -216,6 +237,10 @@ struct hisq_ctx {
     hisq::DevStatus *status = nullptr;
     hisq::SolverWork *solver = nullptr; // cached solver workspace
     hisq::MsWork *msolver = nullptr;    // cached multi-shift workspace
+    // a context that stands for a batch of lattices (hisq_batch): device and host tables;
+    // its Vh is the largest member's, its link stores belong to the members
+    hisq::BatchDesc *batch = nullptr;
+    hisq::BatchDesc *batch_host = nullptr;
 };
 
 struct hisq_field {

@@ -84,6 +84,12 @@ _SIGS = {
     "hisq_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "hisq_cg": (_I, [_P, _D, _P, _P, _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
     "hisq_multishift_cg": (_I, [_P, _D, _I, _P, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
+    "hisq_batch_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "hisq_batch_destroy": (None, [_P]),
+    "hisq_batch_sites": (_L, [_P]),
+    "hisq_batch_last_error_message": (ctypes.c_char_p, [_P]),
+    "hisq_batch_dslash": (_I, [_P, _I, _P, _P, _I, _P]),
+    "hisq_batch_cg": (_I, [_P, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
     "hisq_net_opts_default": (None, [ctypes.POINTER(NetOpts)]),
     "hisq_net_create": (_I, [_P, ctypes.POINTER(NetOpts), ctypes.POINTER(_P)]),
     "hisq_net_destroy": (None, [_P]),
@@ -226,6 +232,53 @@ class Context:
         tp = (ctypes.c_double * n)(*tol) if tol is not None else None
         rc = self.check(lib().hisq_multishift_cg(self.h, float(m), n, sig, _ptr(b), xp, tp, ctypes.byref(o),
                                                  ctypes.byref(st), _ptr(residuals)))
+        return rc, st
+
+
+class Batch:
+    """Lattices of different sizes in single launches (hisq_batch_*).  Vectors are packed:
+    lattice k's [Vh_k][3] complex sites follow those of lattices 0..k-1."""
+
+    def __init__(self, ctxs):
+        self.ctxs = list(ctxs)  # the batch borrows the contexts
+        arr = (ctypes.c_void_p * len(self.ctxs))(*[c.h.value for c in self.ctxs])
+        h = ctypes.c_void_p()
+        rc = lib().hisq_batch_create(ctypes.byref(h), len(self.ctxs), arr)
+        if rc != OK:
+            raise HisqError(rc, lib().hisq_strerror(rc).decode())
+        self.h = h
+        self.sites = lib().hisq_batch_sites(h)
+        self.offsets = []
+        off = 0
+        for c in self.ctxs:
+            self.offsets.append(off)
+            off += c.Vh
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hisq_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc):
+        if rc not in (OK, ENOTCONVERGED):
+            raise HisqError(rc, lib().hisq_batch_last_error_message(self.h).decode())
+        return rc
+
+    def dslash(self, out_parity, inp, out, prec=F64, stream=None):
+        return self.check(lib().hisq_batch_dslash(self.h, out_parity, _ptr(inp), _ptr(out), prec, _stream(stream)))
+
+    def cg(self, masses, b, x, opts=None, residuals=None, **kw):
+        o = opts or Context.solve_opts(**kw)
+        st = Stats()
+        m = (ctypes.c_double * len(self.ctxs))(*[float(v) for v in masses])
+        rc = self.check(lib().hisq_batch_cg(self.h, m, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(st),
+                                            _ptr(residuals)))
         return rc, st
 
 

@@ -2,6 +2,7 @@
 
   python -m paper_2306_01098_gb300.solver_bench --workload batched   # 64^3 x 16
   python -m paper_2306_01098_gb300.solver_bench --workload large     # 96^3 x 24, 12-real links
+  python -m paper_2306_01098_gb300.solver_bench --workload uneven    # 32 uneven lattices, batched
 
 batched: multi-RHS CG for nrhs in {1, 4, 8, 16} (16-bit links, FP32 vectors, FP64 reliable
          updates), time per right-hand side against plain FP64 CG with one right-hand side, and
@@ -107,12 +108,70 @@ def large(reps=1):
     return rows
 
 
+def uneven(reps=3):
+    """32 uneven lattices (8^3x8 ... 24^3x8, eps 0.3, m 0.1, 1 source each, FP32 sloppy
+    with FP64 reliable updates): one batched Dslash launch against 32 launches, and the
+    batched CG (one graph, all members per launch) against 32 solves one after another."""
+    import torch
+
+    from hisq_inputs import fields, workloads
+    from paper_2306_01098_gb300 import hisq
+    dims = workloads.uneven_batch()
+    ctxs = []
+    for i, d in enumerate(dims):
+        fat, lng = fields.recipe_links(d, 0.3, 1100 + i, device="cuda")
+        ctxs.append(hisq.Context(d, fat, lng, precs=(hisq.F64, hisq.F32)))
+    batch = hisq.Batch(ctxs)
+    bs = [fields.gaussian_source(d, 2200 + i, device="cuda")[0] for i, d in enumerate(dims)]
+    bp = torch.cat([b.reshape(-1) for b in bs]).reshape(-1, 3)
+    out = torch.empty_like(bp)
+    outs = [torch.empty_like(b) for b in bs]
+    rows = [{"lattices": len(dims), "sites": 2 * batch.sites}]
+
+    def dslash_batched():
+        batch.dslash(0, bp, out, prec=hisq.F32)
+
+    def dslash_each():
+        for c, b, o in zip(ctxs, bs, outs):
+            c.dslash(0, b, o, prec=hisq.F32)
+
+    for name, fn in (("batched", dslash_batched), ("per_lattice", dslash_each)):
+        fn()
+        ms, _ = _timed(lambda: [fn() for _ in range(10)], reps)
+        rows.append({"op": "dslash_f32_with_conversions", "mode": name, "ms": ms / 10})
+    kw = dict(tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, reliable_delta=0.01)
+    x = torch.zeros_like(bp)
+    res = torch.zeros(len(dims), dtype=torch.float64)
+    batch.cg([0.1] * len(dims), bp, x.zero_(), residuals=res, **kw)
+    ms, (rc, st) = _timed(lambda: batch.cg([0.1] * len(dims), bp, x.zero_(), residuals=res, **kw), reps)
+    rows.append({"solve": "cg", "mode": "batched", "ms": ms, "iterations": st.iterations,
+                 "max_true_residual": float(res.max()), "rc": rc})
+    xs = [torch.zeros_like(b) for b in bs]
+
+    def each():
+        worst, its = 0.0, 0
+        for c, b, xk in zip(ctxs, bs, xs):
+            r1 = torch.zeros(1, dtype=torch.float64)
+            rc1, st1 = c.cg(0.1, b, xk.zero_(), residuals=r1, **kw)
+            worst, its = max(worst, float(r1[0])), max(its, st1.iterations)
+        return worst, its
+
+    each()
+    ms1, (worst, its) = _timed(each, reps)
+    rows.append({"solve": "cg", "mode": "per_lattice", "ms": ms1, "max_iterations": its, "max_true_residual": worst,
+                 "speedup_batched": ms1 / ms})
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["batched", "large"], default="batched")
+    ap.add_argument("--workload", choices=["batched", "large", "uneven"], default="batched")
     ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args()
-    rows = batched(a.reps) if a.workload == "batched" else large(a.reps)
+    rows = {"batched": batched, "large": large, "uneven": uneven}[a.workload](a.reps)
     for r in rows:
         print(json.dumps(r), flush=True)
 
