@@ -23,7 +23,7 @@ _lib = None
 __all__ = [
     "build", "lib", "dslash", "dslash_site", "mdagm", "cg", "cg_fixed", "multishift_cg",
     "phase_links", "eo_index", "coords", "count_site", "net_layer", "net_layer_backward",
-    "net_apply", "net_loss_grad", "fcg", "fcg_dense", "dense_A", "dense_D", "NTAP",
+    "net_apply", "net_loss_grad", "net_loss_grad_residual", "fcg", "fcg_dense", "dense_A", "dense_D", "NTAP",
     "set_threads",
 ]
 
@@ -230,6 +230,45 @@ def net_loss_grad(dims, fat, lng, chans, w, b_even, x_even, phased=False):
     loss = lib().ho_net_loss_grad(_ptr(d), _ptr(F), _ptr(W), int(phased), len(chans) - 1, _ptr(ch),
                                   _ptr(ww), _ptr(b), _ptr(x), _ptr(gw))
     return loss, gw
+
+
+def net_loss_grad_residual(dims, fat, lng, chans, w, b_even, x_even, m, phased=False):
+    """Residual-norm loss |A (K b - x)|^2 / |b|^2 of one pair and its weight gradient.
+
+    A = 4 m^2 - D_eo D_oe.  The forward pass runs the layers on the full lattice (b on the
+    even sites, zero on the odd ones) and keeps the even sites of the output, z = K b.
+    With e = z - x the gradient with respect to the output is 2 A^2 e / |b|^2 (A is
+    Hermitian), zero on odd sites, and is carried back through the layers with
+    net_layer_backward.  Gradients use the convention d/dRe + i d/dIm, as net_loss_grad.
+    """
+    V = _vol(dims)
+    Vh = V // 2
+    b = np.asarray(b_even, dtype=np.complex128).reshape(Vh, 3)
+    x = np.asarray(x_even, dtype=np.complex128).reshape(Vh, 3)
+    w = np.asarray(w, dtype=np.complex128)
+    nl = len(chans) - 1
+    acts = [np.zeros((1, V, 3), dtype=np.complex128)]
+    acts[0][0, :Vh] = b
+    ws, off = [], 0
+    for l in range(nl):
+        n = NTAP * chans[l + 1] * chans[l]
+        ws.append(w[off:off + n].reshape(NTAP, chans[l + 1], chans[l]))
+        off += n
+        acts.append(net_layer(dims, fat, lng, ws[l], acts[l], chans[l], chans[l + 1], phased))
+    e = acts[-1][0, :Vh] - x
+    Ae = mdagm(dims, fat, lng, m, e, phased=phased)
+    A2e = mdagm(dims, fat, lng, m, Ae, phased=phased)
+    bb = float(np.vdot(b, b).real)
+    loss = float(np.vdot(Ae, Ae).real) / bb
+    g = np.zeros((1, V, 3), dtype=np.complex128)
+    g[0, :Vh] = 2.0 * A2e / bb
+    grads = [None] * nl
+    for l in reversed(range(nl)):
+        gin, gw = net_layer_backward(dims, fat, lng, ws[l], acts[l], g, chans[l], chans[l + 1], phased,
+                                     want_gin=l > 0)
+        grads[l] = gw.reshape(-1)
+        g = gin
+    return loss, np.concatenate(grads)
 
 
 def fcg(dims, fat, lng, m, b, chans=None, w=None, tol=1e-10, maxiter=100000, phased=False):

@@ -5,7 +5,9 @@ layer stated in the oracle.  Pins:
   * a single layer with tap weights (+1, -1) reproduces D on both parities (ties the
     transports to the independently pinned Dslash);
   * gauge covariance of the whole network under a random SU(3) transform;
-  * the backward pass against central finite differences of the loss (FP64);
+  * the backward pass against central finite differences of the loss (FP64), for the
+    error-norm loss and the residual-norm loss; the residual-norm gradient of a single
+    identity tap against its closed form with the dense operator;
   * flexible CG with K = identity reproduces CG; with K = dense A^{-1} it converges in
     one iteration.
 """
@@ -98,6 +100,55 @@ def test_backward_matches_finite_differences(chans):
             fd = (lp - lm) / (2 * h)
             an = g[i].real if part == "re" else g[i].imag
             assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)), (i, part, fd, an)
+
+
+def test_residual_loss_single_tap_closed_form():
+    # K = c * identity (one 1 -> 1 layer, tap 0 only): L(c) = |A (c b - x)|^2 / |b|^2 and
+    # dL/dRe c + i dL/dIm c = 2 <b, A^2 (c b - x)> / |b|^2
+    dims, m = (4, 4, 4, 6), 0.1
+    fat, lng = _links(dims, seed=46)
+    b = _np(fields.gaussian_source(dims, 93))[0]
+    x = _np(fields.gaussian_source(dims, 94))[0]
+    c = 0.7 - 0.2j
+    w = np.zeros(NTAP, dtype=np.complex128)
+    w[0] = c
+    loss, g = oracle.net_loss_grad_residual(dims, fat, lng, [1, 1], w, b, x, m)
+    A = oracle.dense_A(dims, fat, lng, m)
+    bv, xv = b.reshape(-1), x.reshape(-1)
+    e = c * bv - xv
+    bb = np.vdot(bv, bv).real
+    assert abs(loss - np.linalg.norm(A @ e) ** 2 / bb) <= 1e-12 * loss
+    want = 2 * np.vdot(bv, A @ (A @ e)) / bb
+    assert abs(g[0] - want) <= 1e-12 * abs(want)
+    # every hop changes parity: in one layer the hopping taps only reach odd output sites,
+    # which the loss does not see
+    assert np.abs(g[1:]).max() == 0.0
+
+
+@pytest.mark.parametrize("chans", [[1, 2, 1], [1, 3, 2, 1]])
+def test_residual_loss_backward_matches_finite_differences(chans):
+    dims, m = (4, 4, 4, 4), 0.2
+    fat, lng = _links(dims, seed=47)
+    w = _rand_weights(chans, 8)
+    b = _np(fields.gaussian_source(dims, 95))[0]
+    x = _np(fields.gaussian_source(dims, 96))[0]
+    loss, g = oracle.net_loss_grad_residual(dims, fat, lng, chans, w, b, x, m)
+    z = oracle.net_apply(dims, fat, lng, chans, w, b)
+    r = oracle.mdagm(dims, fat, lng, m, z - x)
+    assert abs(loss - np.linalg.norm(r) ** 2 / np.linalg.norm(b) ** 2) <= 1e-12 * loss
+    rng = np.random.default_rng(1)
+    idx = rng.choice(w.size, size=10, replace=False)
+    h = 1e-5
+    for i in idx:
+        for part, unit in (("re", 1.0), ("im", 1j)):
+            wp, wm = w.copy(), w.copy()
+            wp[i] += h * unit
+            wm[i] -= h * unit
+            lp, _ = oracle.net_loss_grad_residual(dims, fat, lng, chans, wp, b, x, m)
+            lm, _ = oracle.net_loss_grad_residual(dims, fat, lng, chans, wm, b, x, m)
+            fd = (lp - lm) / (2 * h)
+            an = g[i].real if part == "re" else g[i].imag
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (i, part, fd, an)
 
 
 def test_fcg_identity_reproduces_cg():
