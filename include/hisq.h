@@ -269,11 +269,18 @@ typedef struct {
     double lr, beta1, beta2, eps; /* Adam (default 2e-3, 0.9, 0.999, 1e-8)                  */
     double init_hop;       /* scale of the random hopping weights at initialisation (0.05)  */
     unsigned long long seed; /* initialisation and shuffling seed                           */
+    int loss;              /* training loss per pair: 0 (default) error norm |K b - x|^2 /
+                              |x|^2; 1 residual norm |A (K b - x)|^2 / |b|^2 with
+                              A = 4 mass^2 - D_eo D_oe applied with the FP64 links (which the
+                              context must hold)                                             */
+    double mass;           /* mass of A for loss 1                                           */
 } hisq_net_opts;
 
 void hisq_net_opts_default(hisq_net_opts *opts);
 /* Create a network on a context (the context must hold 18-real links of opts->link_prec).
- * Weights start as the identity map plus small random hopping weights. */
+ * Weights start as the identity map plus small random hopping weights.  The network uses
+ * the context's link stores: every call but hisq_net_destroy needs the context alive;
+ * hisq_net_destroy may run before or after hisq_destroy of the context. */
 int hisq_net_create(hisq_ctx *ctx, const hisq_net_opts *opts, hisq_net **net);
 void hisq_net_destroy(hisq_net *net);
 /* number of complex weights, and host copies of them (interleaved re, im doubles) */

@@ -26,6 +26,9 @@
 
 namespace hisq {
 
+int apply_mdagm(hisq_ctx *ctx, int prec, double m, const void *in, void *tmp, void *out, int nrhs, size_t rhs_bytes,
+                cudaStream_t st, const Reduce *red, bool tune);
+
 // ---------------------------------------------------------------- activation access
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
@@ -343,6 +346,43 @@ __global__ void k_net_loss_grad(const uint32_t *zact, const double *x, uint32_t 
     }
 }
 
+// residual-loss pieces: |A e|^2 and |b|^2 (FIN_STORE values 0, 1)
+__global__ void k_net_loss_res(const double *Ae, const double *b, uint32_t Vh, Reduce red)
+{
+    double rr = 0.0, bb = 0.0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < Vh; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            const double a = Ae[(size_t)i * 6 + k], c = b[(size_t)i * 6 + k];
+            rr += a * a;
+            bb += c * c;
+        }
+    }
+    double mine[2] = {rr, bb};
+    block_sum_multi<2>(mine);
+    grid_reduce<2>(red, mine, 2, 0, 2, blockIdx.x);
+}
+
+// e = z - x (canonical FP64)
+__global__ void k_net_sub(const double *z, const double *x, double *e, size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) e[i] = z[i] - x[i];
+}
+
+// g = weight * 2 A^2 e / |b|^2 on even sites, 0 on odd sites (1-channel BF16)
+__global__ void k_net_grad_res(const double *A2e, uint32_t *g, uint32_t Vh, const Scalars *sc, double weight)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * Vh) return;
+    const double f = weight * 2.0 / sc[1].last;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        g[(size_t)i * 3 + k] = i < Vh ? bf_pack((float)(f * A2e[(size_t)i * 6 + 2 * k]),
+                                                (float)(f * A2e[(size_t)i * 6 + 2 * k + 1]))
+                                      : 0u;
+}
+
 // ---------------------------------------------------------------- launch helpers
 template <int PL>
 static cudaError_t launch_layer_pl(const NetLayerArgs &a, int cin, int cout, cudaStream_t st)
@@ -436,8 +476,10 @@ int net_forward(hisq_net *n, const double *b, double *z, cudaStream_t st)
 // one (b, x) pair: forward, loss, gradient accumulated into n->grad (weight `scale`)
 int net_accumulate(hisq_net *n, const double *b, const double *x, double scale, cudaStream_t st)
 {
-    const uint32_t Vh = n->ctx->g.Vh, V = 2 * Vh;
-    int rc = net_forward(n, b, nullptr, st);
+    hisq_ctx *ctx = n->ctx;
+    const uint32_t Vh = ctx->g.Vh, V = 2 * Vh;
+    const bool res = n->opts.loss == 1;
+    int rc = net_forward(n, b, res ? n->zb : nullptr, st);
     if (rc) return rc;
     Reduce R;
     R.partials = n->partials;
@@ -446,8 +488,19 @@ int net_accumulate(hisq_net *n, const double *b, const double *x, double scale, 
     R.op = FIN_STORE;
     R.nblocks = n->nblk_vec;
     R.ntotal = n->nblk_vec;
-    k_net_loss<<<n->nblk_vec, kVecBlock, 0, st>>>(n->act[n->nlayer], x, Vh, R);
-    k_net_loss_grad<<<(V + 255) / 256, 256, 0, st>>>(n->act[n->nlayer], x, n->gact[0], Vh, n->sc, scale);
+    if (res) { // e = K b - x; loss |A e|^2 / |b|^2; output gradient 2 A^2 e / |b|^2
+        const size_t nd = (size_t)Vh * 6;
+        k_net_sub<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(n->zb, x, n->eb, nd);
+        const size_t rb = (size_t)Vh * 48;
+        const double m = n->opts.mass;
+        if ((rc = apply_mdagm(ctx, HISQ_F64, m, n->eb, n->tb, n->Aeb, 1, rb, st, nullptr, true))) return rc;
+        if ((rc = apply_mdagm(ctx, HISQ_F64, m, n->Aeb, n->tb, n->A2eb, 1, rb, st, nullptr, true))) return rc;
+        k_net_loss_res<<<n->nblk_vec, kVecBlock, 0, st>>>(n->Aeb, b, Vh, R);
+        k_net_grad_res<<<(V + 255) / 256, 256, 0, st>>>(n->A2eb, n->gact[0], Vh, n->sc, scale);
+    } else {
+        k_net_loss<<<n->nblk_vec, kVecBlock, 0, st>>>(n->act[n->nlayer], x, Vh, R);
+        k_net_loss_grad<<<(V + 255) / 256, 256, 0, st>>>(n->act[n->nlayer], x, n->gact[0], Vh, n->sc, scale);
+    }
     HISQ_CUDA(n->ctx, cudaGetLastError());
     uint32_t *g = n->gact[0], *gnext = n->gact[1];
     for (int l = n->nlayer - 1; l >= 0; l--) {

@@ -18,6 +18,7 @@ bool net_shape_supported(int cin, int cout);
 
 struct hisq_net {
     hisq_ctx *ctx = nullptr;
+    int device = 0; // the context's device (teardown does not read the context)
     hisq_net_opts opts{};
     int nlayer = 0;
     int chans[hisq::kNetMaxLayers + 1] = {};
@@ -33,6 +34,7 @@ struct hisq_net {
     unsigned *counter = nullptr;
     hisq::Scalars *sc = nullptr, *h_sc = nullptr;
     double *lossacc = nullptr;
+    double *zb = nullptr, *eb = nullptr, *tb = nullptr, *Aeb = nullptr, *A2eb = nullptr; // loss 1 (FP64)
     int nblk_vec = 0;
     int step = 0;
     cudaStream_t st = nullptr;

@@ -126,16 +126,28 @@ __global__ void k_fcg_p(double2 *p, const double2 *z, size_t n, double br, doubl
     }
 }
 
+// the dot products of one flexible-CG step in one pass (FIN_STORE values): 0 |rn|^2,
+// 1 + 2i <rn - r, z>, 3 + 4i <rn, z>, with <a, b> = sum conj(a) b
+__global__ void k_fcg_dots(const double2 *rn, const double2 *r, const double2 *z, size_t n, Reduce red)
+{
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 a = rn[i], b = r[i], c = z[i];
+        const double dx = a.x - b.x, dy = a.y - b.y;
+        v[0] += a.x * a.x + a.y * a.y;
+        v[1] += dx * c.x + dy * c.y;
+        v[2] += dx * c.y - dy * c.x;
+        v[3] += a.x * c.x + a.y * c.y;
+        v[4] += a.x * c.y - a.y * c.x;
+    }
+    block_sum_multi<5>(v);
+    grid_reduce<5>(red, v, 5, 0, 5, blockIdx.x);
+}
+
 __global__ void k_sub(const double2 *a, const double2 *b, double2 *c, size_t n)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         c[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
-}
-
-__global__ void k_finite(const double *v, size_t n, int *bad)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        if (!isfinite(v[i])) *bad = 1;
 }
 
 }  // namespace hisq
@@ -173,8 +185,14 @@ int hisq_net_create(hisq_ctx *ctx, const hisq_net_opts *opts_in, hisq_net **out)
     if (o.link_prec != HISQ_F32 && o.link_prec != HISQ_F16) return set_error(ctx, HISQ_EINVAL, "hisq_net_create: link precision");
     if (!ctx->links[o.link_prec].built || ctx->links[o.link_prec].nreal != 18)
         return set_error(ctx, HISQ_ENOTBUILT, "hisq_net_create: needs 18-real links of that precision");
+    if (o.loss != 0 && o.loss != 1) return set_error(ctx, HISQ_EINVAL, "hisq_net_create: loss");
+    if (o.loss == 1 && !(o.mass >= 0.0 && std::isfinite(o.mass)))
+        return set_error(ctx, HISQ_EINVAL, "hisq_net_create: mass");
+    if (o.loss == 1 && !ctx->links[HISQ_F64].built)
+        return set_error(ctx, HISQ_ENOTBUILT, "hisq_net_create: the residual loss needs the FP64 links");
     hisq_net *n = new hisq_net();
     n->ctx = ctx;
+    n->device = ctx->device;
     n->opts = o;
     n->nlayer = o.nlayer;
     n->link_prec = o.link_prec;
@@ -210,6 +228,8 @@ int hisq_net_create(hisq_ctx *ctx, const hisq_net_opts *opts_in, hisq_net **out)
     A((void **)&n->counter, 64);
     A((void **)&n->sc, sizeof(Scalars) * 4);
     A((void **)&n->lossacc, sizeof(double));
+    if (o.loss == 1)
+        for (double **q : {&n->zb, &n->eb, &n->tb, &n->Aeb, &n->A2eb}) A((void **)q, (size_t)ctx->g.Vh * 48);
     if (rc) {
         net_free(n);
         return rc;
@@ -233,7 +253,7 @@ int hisq_net_create(hisq_ctx *ctx, const hisq_net_opts *opts_in, hisq_net **out)
 void hisq_net_destroy(hisq_net *n)
 {
     if (!n) return;
-    cudaSetDevice(n->ctx->device);
+    cudaSetDevice(n->device);
     cudaDeviceSynchronize();
     net_free(n);
 }
@@ -412,17 +432,16 @@ int hisq_fcg(hisq_ctx *ctx, double m, hisq_net *net, const double *b, double *x,
     auto release = [&]() {
         for (void *p : mem) cudaFree(p);
     };
-    char *r = A(vb), *rn = A(vb), *z = A(vb), *p = A(vb), *q = A(vb), *t = A(vb), *dr = A(vb);
+    char *r = A(vb), *rn = A(vb), *z = A(vb), *p = A(vb), *q = A(vb), *t = A(vb);
     char *xx = A(pb), *tx = A(pb), *Ax = A(pb);
     double *partials = (double *)A(sizeof(double) * 8 * 4096);
     unsigned *counter = (unsigned *)A(64);
-    Scalars *sc = (Scalars *)A(sizeof(Scalars) * 4);
-    int *bad = (int *)A(sizeof(int));
-    if (!r || !rn || !z || !p || !q || !t || !dr || !xx || !tx || !Ax || !partials || !counter || !sc || !bad) {
+    Scalars *sc = (Scalars *)A(sizeof(Scalars) * 8);
+    if (!r || !rn || !z || !p || !q || !t || !xx || !tx || !Ax || !partials || !counter || !sc) {
         release();
         return set_error(ctx, HISQ_ENOMEM, "hisq_fcg: workspace");
     }
-    Scalars hsc[4];
+    Scalars hsc[8];
     cudaStream_t st = (cudaStream_t)o.stream;
     const int nblk = (int)std::min<size_t>((Vh + kVecBlock - 1) / kVecBlock, 4ull * ctx->sm_count);
     Reduce R;
@@ -453,21 +472,27 @@ int hisq_fcg(hisq_ctx *ctx, double m, hisq_net *net, const double *b, double *x,
     const int gb = (int)std::min<size_t>((nc + 255) / 256, 8ull * ctx->sm_count);
     bool use_net = net != nullptr;
     int fallbacks = 0;
+    // z = K(in) (identity once the network is dropped); a non-finite network output is
+    // caught by the dot products that follow
     auto precond = [&](const char *in, char *out) -> int {
-        if (use_net) {
-            int rc = net_forward(net, (const double *)in, (double *)out, st);
-            if (rc) return rc;
-            cudaMemsetAsync(bad, 0, sizeof(int), st);
-            k_finite<<<gb, 256, 0, st>>>((const double *)out, nc * 2, bad);
-            int hb = 0;
-            cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
-            cudaStreamSynchronize(st);
-            if (!hb) return HISQ_OK;
-            use_net = false;
-            fallbacks++;
-        }
+        if (use_net) return net_forward(net, (const double *)in, (double *)out, st);
         return cudaMemcpyAsync(out, in, vb, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? HISQ_OK
                                                                                             : cuda_error(ctx, cudaErrorUnknown, "copy");
+    };
+    auto step_dots = [&](const char *a, const char *c, const char *zz, double (&v)[5]) -> int {
+        Reduce Q = R;
+        Q.op = FIN_STORE;
+        k_fcg_dots<<<nblk, kVecBlock, 0, st>>>((const double2 *)a, (const double2 *)c, (const double2 *)zz, nc, Q);
+        if (cudaMemcpyAsync(hsc, sc, sizeof(Scalars) * 5, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return cuda_error(ctx, cudaGetLastError(), "hisq_fcg: reduction");
+        for (int i = 0; i < 5; i++) v[i] = hsc[i].last;
+        return HISQ_OK;
+    };
+    auto all_finite = [](const double (&v)[5]) {
+        for (double a : v)
+            if (!std::isfinite(a)) return false;
+        return true;
     };
     int rc = HISQ_OK;
     double bb, tmp;
@@ -477,9 +502,14 @@ int hisq_fcg(hisq_ctx *ctx, double m, hisq_net *net, const double *b, double *x,
     if ((rc = applyA(pa, (const char *)x, q))) { release(); return rc; }
     k_sub<<<gb, 256, 0, st>>>((const double2 *)b, (const double2 *)q, (double2 *)r, nc);
     if ((rc = precond(r, z))) { release(); return rc; }
-    cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, st);
     double rz_re, rz_im, rr;
     if ((rc = dot(r, z, rz_re, rz_im)) || (rc = dot(r, r, rr, tmp))) { release(); return rc; }
+    if (use_net && !(std::isfinite(rz_re) && std::isfinite(rz_im))) { // network output not finite
+        use_net = false;
+        fallbacks++;
+        if ((rc = precond(r, z)) || (rc = dot(r, z, rz_re, rz_im))) { release(); return rc; }
+    }
+    cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, st);
     int it = 0, since_best = 0;
     double best = rr;
     const double stop = o.tol * o.tol * bb;
@@ -494,7 +524,17 @@ int hisq_fcg(hisq_ctx *ctx, double m, hisq_net *net, const double *b, double *x,
         k_fcg_update<<<gb, 256, 0, st>>>((double2 *)x, (const double2 *)p, (const double2 *)q, (const double2 *)r,
                                          (double2 *)rn, nc, ar, ai);
         it++;
-        if ((rc = dot(rn, rn, rr, tmp))) break;
+        // z' = K r'; |r'|^2, <r' - r, z'>, <r', z'> in one pass
+        if ((rc = precond(rn, z))) break;
+        double v[5];
+        if ((rc = step_dots(rn, r, z, v))) break;
+        if (use_net && !all_finite(v)) { // drop the network, continue with K = identity
+            use_net = false;
+            fallbacks++;
+            if ((rc = precond(rn, z)) || (rc = step_dots(rn, r, z, v))) break;
+        }
+        rr = v[0];
+        if (!std::isfinite(rr)) { rc = HISQ_ENOTCONVERGED; break; }
         if (rr < best) { best = rr; since_best = 0; }
         else if (++since_best >= 50 && use_net) { use_net = false; fallbacks++; since_best = 0; }
         if (rr <= stop) {
@@ -511,16 +551,14 @@ int hisq_fcg(hisq_ctx *ctx, double m, hisq_net *net, const double *b, double *x,
             if ((rc = dot(r, z, rz_re, rz_im))) break;
             continue;
         }
-        if ((rc = precond(rn, z))) break;
-        // beta = <r' - r, z'> / <r, z>
-        k_sub<<<gb, 256, 0, st>>>((const double2 *)rn, (const double2 *)r, (double2 *)dr, nc);
-        double nr, ni;
-        if ((rc = dot(dr, z, nr, ni))) break;
+        // beta = <r' - r, z'> / <r, z>  (Polak-Ribiere)
+        const double nr = v[1], ni = v[2];
         const double den = rz_re * rz_re + rz_im * rz_im;
         const double br = (nr * rz_re + ni * rz_im) / den, bi = (ni * rz_re - nr * rz_im) / den;
         k_fcg_p<<<gb, 256, 0, st>>>((double2 *)p, (const double2 *)z, nc, br, bi);
         std::swap(r, rn);
-        if ((rc = dot(r, z, rz_re, rz_im))) break;
+        rz_re = v[3];
+        rz_im = v[4];
     }
     cudaStreamSynchronize(st);
     release();

@@ -58,7 +58,8 @@ class NetOpts(ctypes.Structure):
     _fields_ = [("nlayer", ctypes.c_int), ("channels", ctypes.c_int), ("link_prec", ctypes.c_int),
                 ("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
-                ("init_hop", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+                ("init_hop", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("loss", ctypes.c_int),
+                ("mass", ctypes.c_double)]
 
 
 _P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long

@@ -1,10 +1,11 @@
 """Learned preconditioner on the 32^3 x 8 workload (eps 0.5, m 0.005): train, then compare.
 
-  python -m paper_2306_01098_gb300.precond_bench [--pairs 2000] [--epochs 4] [--test 20]
+  python -m paper_2306_01098_gb300.precond_bench [--pairs 2000] [--epochs 4] [--test 20] [--loss 1]
 
 1. training pairs (b, x = A^-1 b): Gaussian sources solved by multi-RHS mixed-precision CG
    (16-bit links, FP64 reliable updates) to 1e-8;
-2. training of the 4-layer, 8-channel network on the GPU (BF16 activations, Adam);
+2. training of the 4-layer network (8 channels by default) on the GPU (BF16 activations,
+   Adam) on the residual norm |A (K b - x)|^2 / |b|^2 (loss 1) or the error norm (loss 0);
 3. on held-out sources, time and iterations to a true residual of 1e-10 for: plain FP64 CG,
    mixed-precision CG, flexible CG without the network, flexible CG with the network.
 Prints JSON lines.
@@ -22,7 +23,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def run(pairs=2000, epochs=4, test=20, batch=8, lr=2e-3, channels=8):
+def run(pairs=2000, epochs=4, test=20, batch=8, lr=2e-3, channels=8, loss=1):
     import numpy as np
     import torch
 
@@ -48,11 +49,12 @@ def run(pairs=2000, epochs=4, test=20, batch=8, lr=2e-3, channels=8):
     torch.cuda.synchronize()
     out.append({"step": "pairs", "pairs": pairs, "seconds": time.perf_counter() - t0, "mean_iterations": float(np.mean(its))})
     # 2. training
-    net = hisq.Net(ctx, epochs=epochs, batch=batch, lr=lr, channels=channels)
+    net = hisq.Net(ctx, epochs=epochs, batch=batch, lr=lr, channels=channels, loss=loss, mass=w.mass)
     t0 = time.perf_counter()
     losses = net.train(B, X, epochs)
     torch.cuda.synchronize()
-    out.append({"step": "train", "epochs": epochs, "batch": batch, "seconds": time.perf_counter() - t0,
+    out.append({"step": "train", "loss": ["error", "residual"][loss], "channels": channels, "epochs": epochs,
+                "batch": batch, "lr": lr, "seconds": time.perf_counter() - t0,
                 "loss_per_epoch": [float(v) for v in losses], "weights": net.nw})
     del B, X
     torch.cuda.empty_cache()
@@ -71,7 +73,7 @@ def run(pairs=2000, epochs=4, test=20, batch=8, lr=2e-3, channels=8):
     out.append({"step": "apply", "ms": e0.elapsed_time(e1) / 10})
     # 3. held-out comparison
     Bt = fields.gaussian_source(w.dims, w.source_seed + 9000, test, device="cuda")
-    rows = {k: [] for k in ("cg_f64", "cg_mixed", "fcg_identity", "fcg_net")}
+    rows = {k: [] for k in ("cg_f64", "cg_mixed", "fcg_identity", "fcg_net", "fcg_net_fp64")}
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -89,6 +91,7 @@ def run(pairs=2000, epochs=4, test=20, batch=8, lr=2e-3, channels=8):
                                         reliable_delta=0.01)),
             ("fcg_identity", lambda: hisq.fcg(ctx, w.mass, bi, x.zero_(), net=None, tol=w.tol, prec_precise=hisq.F64X)),
             ("fcg_net", lambda: hisq.fcg(ctx, w.mass, bi, x.zero_(), net=net, tol=w.tol, prec_precise=hisq.F64X)),
+            ("fcg_net_fp64", lambda: hisq.fcg(ctx, w.mass, bi, x.zero_(), net=net, tol=w.tol, prec_precise=hisq.F64)),
         ):
             rc, st, ms = timed(fn)
             rows[key].append((rc, st.iterations, st.true_residual, ms))
@@ -108,8 +111,9 @@ def main():
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--channels", type=int, default=8)
+    ap.add_argument("--loss", type=int, default=1, choices=[0, 1])
     a = ap.parse_args()
-    for r in run(a.pairs, a.epochs, a.test, a.batch, a.lr, a.channels):
+    for r in run(a.pairs, a.epochs, a.test, a.batch, a.lr, a.channels, a.loss):
         print(json.dumps(r), flush=True)
 
 

@@ -117,3 +117,65 @@ def test_training_lowers_loss_and_fcg_converges():
     rcc, stc = ctx.cg(m, b.cuda(), xc, tol=1e-10, prec_sloppy=hisq.F64)
     assert rc0 == hisq.OK and abs(st0.iterations - stc.iterations) <= 2
     print(f"losses {losses}, FCG(net) {st.iterations} iterations, FCG(1) {st0.iterations}, CG {stc.iterations}")
+
+
+def test_residual_loss_and_gradient_match_oracle(small):
+    dims, ctx, fat, lng = small
+    m = 0.1
+    net = hisq.Net(ctx, loss=1, mass=m)
+    chans = [1, 8, 8, 8, 1]
+    w = rand_weights(chans, 9)
+    net.set_weights(w)
+    b = fields.gaussian_source(dims, 303)[0]
+    x = fields.gaussian_source(dims, 304)[0]
+    loss, g = net.loss_grad(b.cuda(), x.cuda())
+    loss_o, g_o = oracle.net_loss_grad_residual(dims, fat, lng, chans, w, b.numpy(), x.numpy(), m)
+    assert abs(loss - loss_o) <= 3e-2 * loss_o
+    assert rel(g, g_o) <= 6e-2
+    off = 0
+    for l in range(4):
+        n = NTAP * chans[l + 1] * chans[l]
+        assert rel(g[off:off + n], g_o[off:off + n]) <= 8e-2, l
+        off += n
+
+
+def test_residual_loss_training_lowers_fcg_iterations():
+    # trained on the residual norm |A (K b - x)|^2 / |b|^2, the network takes flexible CG to
+    # the FP64 residual 1e-10 in fewer iterations than flexible CG with K = identity (= CG)
+    dims, m = (8, 8, 8, 8), 0.05
+    fat, lng = fields.recipe_links(dims, 0.5, 77)
+    ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=(hisq.F64, hisq.F64X, hisq.F32, hisq.F16))
+    npairs = 64
+    B = fields.gaussian_source(dims, 310, npairs).cuda()
+    X = torch.zeros_like(B)
+    for k in range(0, npairs, 16):
+        rc, st = ctx.cg(m, B[k:k + 16].contiguous(), X[k:k + 16], tol=1e-8, prec_sloppy=hisq.F32,
+                        prec_precise=hisq.F64)
+        assert rc == hisq.OK
+    net = hisq.Net(ctx, epochs=6, batch=8, lr=3e-3, loss=1, mass=m)
+    losses = net.train(B, X, 6)
+    assert np.all(np.isfinite(losses)) and losses[-1] < 0.5 * losses[0]
+    its_net, its_id = [], []
+    for i in range(3):
+        b = fields.gaussian_source(dims, 900 + i)[0]
+        x = torch.zeros_like(b).cuda()
+        rc, st = hisq.fcg(ctx, m, b.cuda(), x, net=net, tol=1e-10, prec_precise=hisq.F64X)
+        assert rc == hisq.OK and st.reliable_updates == 0  # the network was kept throughout
+        r = b.numpy() - oracle.mdagm(dims, fat.numpy(), lng.numpy(), m, x.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(b.numpy()) <= 1e-10
+        its_net.append(st.iterations)
+        rc0, st0 = hisq.fcg(ctx, m, b.cuda(), torch.zeros_like(b).cuda(), net=None, tol=1e-10, prec_precise=hisq.F64X)
+        its_id.append(st0.iterations)
+    print(f"residual-loss training: losses {losses}, FCG(net) {its_net}, FCG(identity) {its_id}")
+    assert max(its_net) < 0.9 * min(its_id)
+
+
+def test_network_may_outlive_its_context():
+    dims = (6, 4, 4, 6)
+    fat, lng = fields.recipe_links(dims, 0.5, 78)
+    ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=(hisq.F64, hisq.F32))
+    net = hisq.Net(ctx)
+    ctx.close()
+    net.close()
+    torch.cuda.synchronize()
+    assert float(torch.ones(4, device="cuda").sum()) == 4.0
