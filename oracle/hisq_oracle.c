@@ -673,11 +673,14 @@ double ho_net_loss_grad(const int dims[4], const double *fat, const double *lng,
 /* ------------------------------------------------------------------ flexible CG */
 
 /*
- * Flexible (inexact-preconditioner) CG with the Polak-Ribiere beta:
+ * Flexible (inexact-preconditioner) CG with the Polak-Ribiere beta, <a, b> = sum conj(a) b:
  *   r = b - A x; z = K r; p = z
- *   repeat: alpha = <r, z> / <p, A p>;  x += alpha p;  r_new = r - alpha A p
+ *   repeat: alpha = conj(<r, z>) / <p, A p>;  x += alpha p;  r_new = r - alpha A p
  *           z_new = K r_new;  beta = <r_new - r, z_new> / <r, z>;  p = z_new + beta p
  * until |r| <= tol |b|.  K is the network above (nlayer > 0) or the identity (nlayer = 0).
+ * alpha minimises the A-norm of the error along p: alpha = <p, r> / <p, A p>, and
+ * <p, r> = <z, r> = conj(<r, z>) because r is orthogonal to the previous direction; beta
+ * makes the new direction A-orthogonal to p.  For a Hermitian K, <r, z> is real.
  * stats: [iterations, iterated |r|/|b|, recomputed |b - A x|/|b|].
  */
 int ho_fcg(const int dims[4], const double *fat, const double *lng, int phased, double m,
@@ -705,7 +708,7 @@ int ho_fcg(const int dims[4], const double *fat, const double *lng, int phased, 
     int k = 0;
     while (k < maxiter && rr > tol * tol * bb) {
         apply_A(&op, p, Ap);
-        cplx alpha = rz / creal(dot(p, Ap, n));
+        cplx alpha = conj(rz) / creal(dot(p, Ap, n));
         for (long i = 0; i < n; i++) {
             x[i] += alpha * p[i];
             rn[i] = r[i] - alpha * Ap[i];
@@ -759,7 +762,7 @@ int ho_fcg_dense(const int dims[4], const double *fat, const double *lng, int ph
     int k = 0;
     while (k < maxiter && rr > tol * tol * bb) {
         apply_A(&op, p, Ap);
-        cplx alpha = rz / creal(dot(p, Ap, n));
+        cplx alpha = conj(rz) / creal(dot(p, Ap, n));
         for (long i = 0; i < n; i++) {
             x[i] += alpha * p[i];
             rn[i] = r[i] - alpha * Ap[i];

@@ -168,3 +168,20 @@ def test_fcg_exact_inverse_converges_in_one_iteration():
     K = np.linalg.inv(A)
     x, it, _, r = oracle.fcg_dense(dims, fat, lng, m, K, b, tol=1e-10)
     assert it == 1 and r < 1e-12
+
+
+def test_fcg_complex_phase_preconditioner_reproduces_cg():
+    # K = exp(i theta) I spans the same Krylov space as K = I, and the step that minimises
+    # the A-norm of the error along p is alpha = <p, r> / <p, A p> = conj(<r, z>) / <p, A p>
+    # (<a, b> = sum conj(a) b): flexible CG must then take CG's steps.  Dropping the
+    # conjugate (alpha = <r, z> / <p, A p>) rotates every step by exp(2 i theta) and fails.
+    dims, m = (4, 4, 4, 4), 0.1
+    fat, lng = _links(dims, seed=47)
+    b = _np(fields.gaussian_source(dims, 95))[0]
+    n = b.size
+    _, it_cg, _, _ = oracle.cg(dims, fat, lng, m, b, tol=1e-10)
+    x1, it1, _, r1 = oracle.fcg_dense(dims, fat, lng, m, np.eye(n, dtype=np.complex128), b, tol=1e-10)
+    K = np.exp(0.7j) * np.eye(n, dtype=np.complex128)
+    x, it, _, r = oracle.fcg_dense(dims, fat, lng, m, K, b, tol=1e-10, maxiter=4 * it_cg)
+    assert r <= 1e-10 and abs(it - it_cg) <= 1 and abs(it1 - it_cg) <= 1
+    assert np.linalg.norm(x - x1) <= 1e-9 * np.linalg.norm(x1)
