@@ -208,7 +208,8 @@ def run_ours(args, world, rank, local):
         precise = precise_default if precise is None else precise
         rc, st = ctx.cg(MASS, bb, xb, tol=TOL, prec_sloppy=prec, prec_precise=precise, reliable_interval=100,
                         l2_persist=int(args.l2_persist), use_graph=int(args.use_graph),
-                        reliable_delta=args.delta, profile=profile, host_buffers=host, stream=stream)
+                        reliable_delta=args.delta, profile=profile, host_buffers=host, stream=stream,
+                        single_reduction=args.single_reduction)
         if rc != hisq.OK:
             raise RuntimeError(f"solve did not converge: {st.as_dict()}")
         return st
@@ -279,7 +280,10 @@ def run_ours(args, world, rank, local):
     Vh = ctx.Vh
     lb = {hisq.F32: 72, hisq.F16: 36, hisq.BF16: 36, hisq.F64X: 144}[sloppy]
     sb = {hisq.F32: 24, hisq.F16: 16, hisq.BF16: 16, hisq.F64X: 48}[sloppy]
-    bytes_per_launch = Vh * (16 * lb + 2 * sb)
+    # mean over the iteration's Dslash pair: every link once, input and output spinor once,
+    # plus the epilogue's reads in D_eo (p, and r in the single-reduction form)
+    epi_reads = 2 if args.single_reduction else 1
+    bytes_per_launch = Vh * (16 * lb + 2 * sb) + Vh * sb * epi_reads // 2
     d_ms = sum(s.dslash_ms for s in stats) / max(1, sum(s.dslash_timed for s in stats))
     hbm, src = peaks()
     achieved = bytes_per_launch / (d_ms * 1e-3) / 1e9
@@ -301,6 +305,7 @@ def run_ours(args, world, rank, local):
                    "l2": "flushed between timed solves (256 MB write)",
                    "l2_persist_links": {-1: "auto", 0: "off", 1: "on"}[args.l2_persist],
                    "iteration_loop": "CUDA graph WHILE node" if args.use_graph else "direct launches",
+                   "reductions_per_iteration": 1 if args.single_reduction else 2,
                    "parallelism": f"replicas x{world}"},
         "iterations": st.iterations, "reliable_updates": st.reliable_updates, "true_residual": st.true_residual,
         "error_vs_fp64": err_vs_fp64, "fp64_cg_ms": fp64_ms, "fp64_iterations": st64.iterations,
@@ -330,6 +335,7 @@ def main():
     ap.add_argument("--l2-persist", type=int, default=-1)
     ap.add_argument("--delta", type=float, default=0.01)
     ap.add_argument("--use-graph", type=int, default=1, help="0: direct launches (for ncu launch lists)")
+    ap.add_argument("--single-reduction", type=int, default=0, help="1: one grid reduction per CG iteration")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash-table", action="store_true")

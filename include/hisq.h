@@ -187,6 +187,12 @@ typedef struct {
                               when the call returns): 1 on, 0 off, -1 (default) when the
                               whole field fits the device's persisting-L2 maximum          */
     void *stream;          /* cudaStream_t (NULL = legacy default stream)                    */
+    int single_reduction;  /* CG: 1: one grid reduction per iteration: the normal operator's
+                              epilogue reduces <p,Ap>, |r|^2, <r,Ap>, <Ap,Ap>, and
+                              |r'|^2 = |r|^2 - 2 alpha <r,Ap> + alpha^2 <Ap,Ap> gives beta
+                              before one pass updates x, r and p (three launches per
+                              iteration); 0 (default): the two-reduction form, |r'|^2
+                              reduced from the updated r (four launches)                   */
 } hisq_solve_opts;
 
 typedef struct {
@@ -263,7 +269,7 @@ typedef struct hisq_net hisq_net;
 typedef struct {
     int nlayer;            /* layers (default 4); channels 1 -> C -> ... -> C -> 1           */
     int channels;          /* hidden complex channels C: 1, 2, 4 or 8 (default 8)           */
-    int link_prec;         /* link store of the transports: HISQ_F32 (default) or HISQ_F16  */
+    int link_prec;         /* link store of the transports: HISQ_F16 (default) or HISQ_F32  */
     int epochs;            /* passes over the training pairs (default 4)                    */
     int batch;             /* pairs per Adam step (default 8)                               */
     double lr, beta1, beta2, eps; /* Adam (default 2e-3, 0.9, 0.999, 1e-8)                  */
@@ -274,6 +280,9 @@ typedef struct {
                               A = 4 mass^2 - D_eo D_oe applied with the FP64 links (which the
                               context must hold)                                             */
     double mass;           /* mass of A for loss 1                                           */
+    int tensor_cores;      /* 1 (default): the channel mixing of the 8 -> 8 layers runs on the
+                              tensor cores (tcgen05, BF16 operands, FP32 accumulation in
+                              tensor memory); 0: FP32 arithmetic on the CUDA cores            */
 } hisq_net_opts;
 
 void hisq_net_opts_default(hisq_net_opts *opts);

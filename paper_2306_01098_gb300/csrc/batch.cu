@@ -65,6 +65,7 @@ static void batch_free(hisq_batch *b)
         cudaDeviceSynchronize();
         release_work(v);
         release_ms_work(v);
+        release_fcg_work(v);
         if (v->ws) cudaFree(v->ws);
         if (v->batch) cudaFree(v->batch);
         delete v->batch_host;

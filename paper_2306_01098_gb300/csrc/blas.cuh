@@ -192,6 +192,47 @@ __global__ void __launch_bounds__(kVecBlock) k_update_xp(VecRef x, VecRef p, Vec
     }
 }
 
+// The update of a single-reduction CG iteration, after the Dslash epilogue's finishing step
+// (FIN_AB) has produced alpha, beta and the flags of this iteration:
+//   x += alpha p ; r -= alpha Ap ; p = r + beta p   (p only in mode 0 and while active)
+// alpha is used only if it was produced by this iteration (astamp == it_all - 1).
+template <int PS, int PX>
+__global__ void __launch_bounds__(kVecBlock) k_update_xrp(VecRef x, VecRef p, VecRef r, VecRef Ap, uint32_t Vh,
+                                                          const Scalars *sc, int mode, const LoopCtl *ctl)
+{
+    if (ctl) mode = ctl->mode;
+    using BS = Blas<PS>;
+    using BX = Blas<PX>;
+    static_assert(std::is_same<typename BS::Vec, typename BX::Vec>::value, "shared vector type");
+    const int rhs = blockIdx.y;
+    const Scalars &S = sc[rhs];
+    const double alpha = alpha_fresh_for_x(S) ? S.alpha : 0.0, beta = S.beta;
+    const bool do_xr = alpha != 0.0;
+    const bool do_p = mode == 0 && S.active;
+    if (!do_xr && !do_p) return;
+    char *xp = x.rhs(rhs), *pp = p.rhs(rhs), *rp = r.rhs(rhs);
+    const char *ap = Ap.rhs(rhs);
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+        typename BS::Vec pv, rv;
+        vload<PS>(pp, s, pv);
+        vload<PS>(rp, s, rv);
+        if (do_xr) {
+            typename BX::Vec xv;
+            typename BS::Vec av;
+            vload<PX>(xp, s, xv);
+            vload<PS>(ap, s, av);
+            BX::axpy(xv, alpha, pv);
+            BS::axpy(rv, -alpha, av);
+            BX::store(xp, s, xv);
+            BS::store(rp, s, rv);
+        }
+        if (do_p) {
+            BS::xpay(pv, rv, beta);
+            BS::store(pp, s, pv);
+        }
+    }
+}
+
 // out (PB) = in (PA), element-wise through double components
 template <int PA, int PB>
 __global__ void __launch_bounds__(kVecBlock) k_convert(VecRef in, VecRef out, uint32_t Vh)

@@ -97,6 +97,11 @@ struct Typed {
         R.cond = cond;
         k_update_r<PS><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.r, w.rbS}, VecRef{w.Ap, w.rbS}, w.Vh, R);
     }
+    static void update_xrp(SolverWork &w, cudaStream_t st, const LoopCtl *ctl)
+    {
+        k_update_xrp<PS, PX><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(
+            VecRef{w.xlo, w.rbX}, VecRef{w.p, w.rbS}, VecRef{w.r, w.rbS}, VecRef{w.Ap, w.rbS}, w.Vh, w.sc, 0, ctl);
+    }
     static void update_xp(SolverWork &w, int mode, cudaStream_t st, const LoopCtl *ctl = nullptr)
     {
         k_update_xp<PS, PX><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(
@@ -222,7 +227,7 @@ int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out)
     char *tmp = nullptr;
     A(&tmp, sizeof(Scalars) * (nrhs + 64));
     W.sc = reinterpret_cast<Scalars *>(tmp);
-    A(&tmp, sizeof(double) * (size_t)(nrhs + 64) * std::max(W.nblk_vec, W.nblk_dslash));
+    A(&tmp, sizeof(double) * (size_t)(4 * nrhs + 64) * std::max(W.nblk_vec, W.nblk_dslash));
     W.partials = reinterpret_cast<double *>(tmp);
     A(&tmp, 64);
     W.counter = reinterpret_cast<unsigned *>(tmp);
@@ -303,7 +308,10 @@ static void set_graph_window(cudaGraph_t g, const cudaAccessPolicyWindow &w)
 }
 
 // ---------------------------------------------------------------- pieces of the iteration
-static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, cudaEvent_t *evs)
+// fused: the D_eo launch carries the single-reduction CG epilogue, whose finishing block
+// also runs the loop control (ctl, cond)
+static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, cudaEvent_t *evs,
+                              bool fused = false, unsigned long long cond = 0)
 {
     const LinkStore &L = ctx->links[w.ps];
     const int nr = w.shape.nr;
@@ -318,19 +326,38 @@ static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream
     b.pv = w.p;
     b.m4 = 4.0 * m * m;
     b.shift = w.shift;
-    b.red = w.red(FIN_ALPHA, 0, 0); // block counts filled in by the launcher
+    b.red = w.red(fused ? FIN_AB : FIN_ALPHA, 0, 0); // block counts filled in by the launcher
+    if (fused) {
+        b.rv = w.r;
+        b.red.ctl = w.ctl;
+        b.red.cond = cond;
+    }
     if (evs) cudaEventRecord(evs[2], st);
-    e = dslash_launch(w.ps, w.pv, 1, b, L.nreal, w.shape, st);
+    e = dslash_launch(w.ps, w.pv, fused ? 2 : 1, b, L.nreal, w.shape, st);
     if (evs) cudaEventRecord(evs[3], st);
     if (e != cudaSuccess) return cuda_error(ctx, e, "sloppy dslash + epilogue");
     return HISQ_OK;
 }
 
 // one iteration: Dslash pair, r update (whose last block also runs the loop control), x/p
-// update (its mode comes from the loop control: p is left alone in a phase's last iteration)
+// update (its mode comes from the loop control: p is left alone in a phase's last iteration).
+// Single-reduction form (w.fused): the D_eo epilogue reduces <p,Ap>, |r|^2, <r,Ap> and
+// <Ap,Ap>; its finishing block produces alpha = |r|^2/<p,Ap>, the next
+// |r - alpha Ap|^2 = |r|^2 - 2 alpha <r,Ap> + alpha^2 <Ap,Ap>, beta and the loop decision, and
+// one pass updates x, r and p: three launches and one grid reduction per iteration instead
+// of four and two.  |r|^2 is taken from the stored r every iteration: carried over from the
+// previous expansion instead, its rounding error (about eps |b|^2) would never decay and the
+// iterated residual could not fall below it.
 static int launch_iteration(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, cudaEvent_t *evs,
                             unsigned long long cond)
 {
+    if (w.fused) {
+        int rc = sloppy_dslash_pair(ctx, w, m, st, evs, true, cond);
+        if (rc) return rc;
+        dispatch(w.pv, [&](auto T) { decltype(T)::update_xrp(w, st, w.ctl); });
+        HISQ_CUDA(ctx, cudaGetLastError());
+        return HISQ_OK;
+    }
     int rc = sloppy_dslash_pair(ctx, w, m, st, evs);
     if (rc) return rc;
     dispatch(w.pv, [&](auto T) {
@@ -471,6 +498,8 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
 
     // before any capture: the shape (timed on the solver's buffers the first time)
     w.shape = dslash_shape(ctx, ps, w.pv, nrhs, w.p, w.t, w.rbS, st);
+    w.fused = o.single_reduction != 0;
+    const long per_it = w.fused ? 3 : 4; // launches per iteration
     const cudaAccessPolicyWindow win = link_window(ctx, ps, o.l2_persist);
     set_stream_window(st, win);
     const int ci = std::max(1, o.check_interval);
@@ -518,14 +547,16 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             if (sample) {
                 if ((rc = launch_iteration(ctx, w, m, st, nullptr, 0))) return rc;
                 if ((rc = launch_iteration(ctx, w, m, st, &w.prof[0], 0))) return rc;
-                kernels += 8;
+                kernels += 2 * per_it;
             }
-            if (!w.graph || w.graph_m != m || w.graph_l2 != (win.num_bytes > 0) || w.graph_shift != w.shift_key) {
+            if (!w.graph || w.graph_m != m || w.graph_l2 != (win.num_bytes > 0) || w.graph_shift != w.shift_key ||
+                w.graph_fused != w.fused) {
                 if (w.graph) { cudaGraphExecDestroy(w.graph); w.graph = nullptr; }
                 if ((rc = build_loop_graph(ctx, w, m, win, st))) return rc;
                 w.graph_m = m;
                 w.graph_shift = w.shift_key;
                 w.graph_l2 = win.num_bytes > 0;
+                w.graph_fused = w.fused;
             }
             HISQ_CUDA(ctx, cudaGraphLaunch(w.graph, st));
         } else {
@@ -536,7 +567,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         const int executed = w.h_sc[0].it_all - it_all; // iterations the device ran in this phase
         it_all = w.h_sc[0].it_all;
         since_ru += executed;
-        kernels += 4L * executed - (o.use_graph && sample ? 8 : 0);
+        kernels += per_it * executed - (o.use_graph && sample ? 2 * per_it : 0);
         int it = 0;
         bool any_active = false, any_flag = false;
         for (int r = 0; r < nrhs; r++) {
@@ -647,6 +678,7 @@ void hisq_solve_opts_default(hisq_solve_opts *o)
     o->reliable_delta = 0.1;
     o->zero_guess = 1;
     o->check_interval = 50;
+    o->single_reduction = 0;
     o->use_graph = 1;
     o->l2_persist = -1;
 }

@@ -34,6 +34,22 @@ int cuda_error(hisq_ctx *ctx, cudaError_t e, const char *what)
     return set_error(ctx, e == cudaErrorMemoryAllocation ? HISQ_ENOMEM : HISQ_ECUDA, m);
 }
 
+// Reads (and clears) the context's device error flag after the work queued on `st`:
+// HISQ_EDEVICE with the recording site if a kernel raised it.
+int check_device_status(hisq_ctx *ctx, cudaStream_t st)
+{
+    if (!ctx || !ctx->status) return HISQ_OK;
+    DevStatus h{};
+    cudaError_t e = cudaMemcpyAsync(&h, ctx->status, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "device status");
+    if (h.error == 0) return HISQ_OK;
+    cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), st);
+    cudaStreamSynchronize(st);
+    return set_error(ctx, HISQ_EDEVICE,
+                     h.where == 1 ? "a bounded wait of the tensor-core network layer ran out" : "device error flag raised");
+}
+
 int ensure_workspace(hisq_ctx *ctx, size_t bytes)
 {
     if (ctx->ws_bytes >= bytes) return HISQ_OK;
@@ -319,6 +335,7 @@ void hisq_destroy(hisq_ctx *ctx)
     cudaDeviceSynchronize();
     release_work(ctx);
     release_ms_work(ctx);
+    release_fcg_work(ctx);
     for (auto &L : ctx->links)
         if (L.base) cudaFree(L.base);
     if (ctx->ws) cudaFree(ctx->ws);

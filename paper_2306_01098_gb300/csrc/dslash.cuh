@@ -19,8 +19,10 @@ struct DslashArgs {
     size_t rhs_bytes;      // bytes between right-hand sides
     int nrhs;
     const Scalars *skip;   // if set: return at once when no right-hand side is active
-    // normal-operator epilogue: out = m4 * pv - D in, <pv, out> reduced
+    // normal-operator epilogue: out = m4 * pv - D in, <pv, out> reduced; with the CG
+    // epilogue (EPI = 2) also <rv, out> and <out, out>
     const char *pv;
+    const char *rv;
     double m4;
     const double *shift;   // optional per right-hand side addition to m4 (device)
     Reduce red;

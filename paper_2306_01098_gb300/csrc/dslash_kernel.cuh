@@ -26,7 +26,9 @@
 //     neighbour spinors (PV) are gathered through L1/L2, where their 16-fold reuse happens.
 //     PL and PV differ only for 16-bit links with FP32 vectors.
 // Optional epilogue (normal operator, Sec. 3.2 applyMdaggM):
-//   out = m4 * p - D in,   and <p, out> reduced in FP64 per right-hand side.
+//   EPI = 1: out = m4 * p - D in,   and <p, out> reduced in FP64 per right-hand side;
+//   EPI = 2: the same and also |r|^2, <r, out> and <out, out> (four values per right-hand
+//            side, from which the CG finishing step gets alpha and the next |r|^2).
 // Batches: one launch over the lattices of a batch, each with its own geometry and links
 // (one right-hand side per lattice); a block finds its lattice in the batch table.
 #pragma once
@@ -39,15 +41,60 @@
 
 namespace hisq {
 
+// dot products per right-hand side reduced by an epilogue
+template <int EPI> struct EpiDots { static constexpr int n = EPI == 2 ? 4 : 1; };
+
+// |v|^2 of a vector: float arithmetic for the float types, double otherwise
+template <class T>
+__device__ __forceinline__ double vec_norm2(const typename T::Vec &v)
+{
+    if constexpr (std::is_same<typename T::Vec, FloatArith::Vec>::value) {
+        float d = 0.f;
+#pragma unroll
+        for (int i = 0; i < 6; i++) d = fmaf(v.v[i], v.v[i], d);
+        return (double)d;
+    } else {
+        double d = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            const double c = T::vcomp(v, i);
+            d = fma(c, c, d);
+        }
+        return d;
+    }
+}
+
+// |o|^2 of an accumulator: float arithmetic for the float types, double otherwise
+template <class T>
+__device__ __forceinline__ double acc_norm2(const typename T::Acc &o)
+{
+    if constexpr (std::is_same<typename T::Acc, FloatArith::Acc>::value) {
+        float d = 0.f;
+#pragma unroll
+        for (int i = 0; i < 6; i++) d = fmaf(o.v[i], o.v[i], d);
+        return (double)d;
+    } else {
+        double d = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            const double c = T::comp(o, i);
+            d = fma(c, c, d);
+        }
+        return d;
+    }
+}
+
 // One work item: the sites of one tile (kDslashBlock threads, DS per site) for the NR
-// right-hand sides whose vectors start at in/out/pv (consecutive right-hand sides
+// right-hand sides whose vectors start at in/out/pv/rv (consecutive right-hand sides
 // a.rhs_bytes apart); geometry g, link store `links`.  Epilogue dot products are added to
-// dots.
+// dots (value j of right-hand side r at dots[r * EpiDots<EPI>::n + j]).
 template <int PL, int PV, int NREAL, int NR, int EPI, int DS>
 __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, const char *links, size_t slot_bytes,
                                             double sc0, double sc1, const char *in, char *outp, const char *pvp,
-                                            const double *m4r, uint32_t tile, double (&dots)[NR])
+                                            const char *rvp, const double *m4r, uint32_t tile,
+                                            double (&dots)[NR * EpiDots<EPI>::n])
 {
+    constexpr int ND = EpiDots<EPI>::n;
     using T = Prec<PV>;  // vectors and arithmetic
     using TL = Prec<PL>; // link storage
     constexpr int LB = NREAL == 18 ? LinkBytes<PL>::b18 : LinkBytes<PL>::b12;
@@ -135,11 +182,18 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
     if (live && part == 0) {
 #pragma unroll
         for (int r = 0; r < NR; r++) {
-            if constexpr (EPI == 1) {
+            if constexpr (EPI >= 1) {
                 typename T::Vec pv;
                 T::load(pvp + (size_t)r * a.rhs_bytes, s, pv);
                 T::mdagm_epilogue(out[r], a.m4 + (m4r ? m4r[r] : 0.0), pv);
-                dots[r] += T::dot(pv, out[r]);
+                dots[r * ND] += T::dot(pv, out[r]);
+                if constexpr (EPI == 2) {
+                    typename T::Vec rv;
+                    T::load(rvp + (size_t)r * a.rhs_bytes, s, rv);
+                    dots[r * ND + 1] += vec_norm2<T>(rv);
+                    dots[r * ND + 2] += T::dot(rv, out[r]);
+                    dots[r * ND + 3] += acc_norm2<T>(out[r]);
+                }
             }
             T::store(outp + (size_t)r * a.rhs_bytes, s, out[r]);
         }
@@ -157,11 +211,24 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
     if (a.skip) { // uniform over the grid: the scalars do not change during the launch
         bool any = false;
         for (int r = 0; r < a.nrhs; r++) any |= a.skip[r].active != 0;
-        if (!any) return;
+        if (!any) {
+            // A launch that carries the loop control (the single-reduction CG epilogue) still
+            // closes the iteration: the iteration stamps advance as the finishing step would
+            // advance them, so no earlier alpha counts as fresh for the update that follows,
+            // and the device loop is told that nothing is active.
+            if constexpr (EPI == 2) {
+                if (a.red.partials && a.red.ctl && blockIdx.x == 0 && threadIdx.x == 0) {
+                    for (int r = 0; r < a.nrhs; r++) a.red.sc[r].it_all++;
+                    finish_control(a.red, a.nrhs);
+                }
+            }
+            return;
+        }
     }
-    double dots[NR];
+    constexpr int ND = EpiDots<EPI>::n;
+    double dots[NR * ND];
 #pragma unroll
-    for (int r = 0; r < NR; r++) dots[r] = 0.0;
+    for (int r = 0; r < NR * ND; r++) dots[r] = 0.0;
     if constexpr (BATCH) {
         __shared__ Geom sg;
         constexpr int d = DS == 1 ? 0 : DS == 2 ? 1 : 2;
@@ -175,15 +242,17 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
         const size_t off = (size_t)k * a.rhs_bytes;
         dslash_item<PL, PV, NREAL, 1, EPI, DS>(a, sg, B.lat[k].links[PL], B.lat[k].slot_bytes[PL], B.lat[k].scale[PL][0],
                                                B.lat[k].scale[PL][1], a.in + off, a.out + off,
-                                               EPI ? a.pv + off : nullptr, a.shift ? a.shift + k : nullptr, tile, dots);
-        if constexpr (EPI == 1) {
+                                               EPI ? a.pv + off : nullptr, EPI == 2 ? a.rv + off : nullptr,
+                                               a.shift ? a.shift + k : nullptr, tile, dots);
+        if constexpr (EPI >= 1) {
             if (a.red.partials) {
-                block_sum_multi<1>(dots);
+                block_sum_multi<ND>(dots);
                 // partials of lattice k beyond its own tiles are zero
                 if (threadIdx.x == 0 && tile == 0)
-                    for (int i = (int)(B.tstart[d][k + 1] - B.tstart[d][k]); i < a.red.nblocks; i++)
-                        a.red.partials[(size_t)k * a.red.nblocks + i] = 0.0;
-                grid_reduce<1>(a.red, dots, 1, k, a.nrhs, (int)tile);
+                    for (int j = 0; j < ND; j++)
+                        for (int i = (int)(B.tstart[d][k + 1] - B.tstart[d][k]); i < a.red.nblocks; i++)
+                            a.red.partials[(size_t)(ND * k + j) * a.red.nblocks + i] = 0.0;
+                grid_reduce<ND>(a.red, dots, ND, ND * k, ND * a.nrhs, (int)tile);
             }
         }
     } else {
@@ -195,11 +264,12 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
         for (uint32_t item = blockIdx.x; item < a.items; item += gridDim.x)
             dslash_item<PL, PV, NREAL, NR, EPI, DS>(a, a.g, a.links, a.slot_bytes, a.scale[0], a.scale[1], a.in + off,
                                                     a.out + off, EPI ? a.pv + off : nullptr,
+                                                    EPI == 2 ? a.rv + off : nullptr,
                                                     a.shift ? a.shift + rhs0 : nullptr, item / ngroups, dots);
-        if constexpr (EPI == 1) {
+        if constexpr (EPI >= 1) {
             if (a.red.partials) { // uniform over the grid
-                block_sum_multi<NR>(dots);
-                grid_reduce<NR>(a.red, dots, NR, rhs0, a.nrhs, (int)(blockIdx.x / ngroups));
+                block_sum_multi<NR * ND>(dots);
+                grid_reduce<NR * ND>(a.red, dots, NR * ND, ND * rhs0, ND * a.nrhs, (int)(blockIdx.x / ngroups));
             }
         }
     }
@@ -289,10 +359,15 @@ static cudaError_t launch_prec(const DslashArgs &a, int nreal, int nr, int ds, c
 }
 
 // instantiate the launcher of one link precision with one vector precision
+// (the CG epilogue, EPI = 2, exists for the vector precisions a solver iterates: not 16-bit)
 #define HISQ_DSLASH_INSTANTIATE(PL, PV)                                                                  \
     cudaError_t dslash_launch_##PL##_##PV(int epi, const DslashArgs &a, int nreal, int nr, int ds,         \
                                           cudaStream_t st)                                               \
     {                                                                                                    \
+        if (epi == 2) {                                                                                  \
+            if constexpr (PV == HISQ_F16 || PV == HISQ_BF16) return cudaErrorInvalidValue;              \
+            else return launch_prec<PL, PV, 2>(a, nreal, nr, ds, st);                                     \
+        }                                                                                                \
         return epi ? launch_prec<PL, PV, 1>(a, nreal, nr, ds, st) : launch_prec<PL, PV, 0>(a, nreal, nr, ds, st); \
     }
 

@@ -187,6 +187,7 @@ struct DevStatus {
 
 struct SolverWork;
 struct MsWork;
+struct FcgWork;
 
 // Dslash launch shape: right-hand sides per thread (N_inner) and threads per site
 struct DslashShape {
@@ -237,6 +238,7 @@ struct hisq_ctx {
     hisq::DevStatus *status = nullptr;
     hisq::SolverWork *solver = nullptr; // cached solver workspace
     hisq::MsWork *msolver = nullptr;    // cached multi-shift workspace
+    hisq::FcgWork *fcg = nullptr;       // cached flexible-CG workspace
     // a context that stands for a batch of lattices (hisq_batch): device and host tables;
     // its Vh is the largest member's, its link stores belong to the members
     hisq::BatchDesc *batch = nullptr;
@@ -258,6 +260,7 @@ int cuda_error(hisq_ctx *ctx, cudaError_t e, const char *what);
 int ensure_workspace(hisq_ctx *ctx, size_t bytes);
 void release_work(hisq_ctx *ctx);
 void release_ms_work(hisq_ctx *ctx);
+void release_fcg_work(hisq_ctx *ctx);
 
 #define HISQ_CUDA(ctx, call)                                      \
     do {                                                          \

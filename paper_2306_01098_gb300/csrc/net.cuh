@@ -37,11 +37,14 @@ struct hisq_net {
     double *zb = nullptr, *eb = nullptr, *tb = nullptr, *Aeb = nullptr, *A2eb = nullptr; // loss 1 (FP64)
     int nblk_vec = 0;
     int step = 0;
+    unsigned long long uid = 0;                  // unique per network (keys cached solver graphs)
     cudaStream_t st = nullptr;
     std::vector<void *> allocs;
 };
 
 namespace hisq {
+// reads and clears the context's device error flag (HISQ_EDEVICE if a kernel raised it)
+int check_device_status(hisq_ctx *ctx, cudaStream_t st);
 int net_forward(hisq_net *n, const double *b, double *z, cudaStream_t st);
 int net_accumulate(hisq_net *n, const double *b, const double *x, double scale, cudaStream_t st);
 }  // namespace hisq

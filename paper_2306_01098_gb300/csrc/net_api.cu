@@ -2,6 +2,7 @@
 // inference, loss gradient, training (Adam), persistence, and flexible CG with K = network.
 #include <algorithm>
 #include <chrono>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -104,52 +105,6 @@ __global__ void k_loss_accum(const Scalars *sc, double *acc)
     *acc += sc[0].last / sc[1].last;
 }
 
-// FCG vector updates with complex coefficients, FP64 canonical vectors
-__global__ void k_fcg_update(double2 *x, const double2 *p, const double2 *q, const double2 *r, double2 *rn, size_t n,
-                             double ar, double ai)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double2 pv = p[i], qv = q[i], rv = r[i];
-        double2 xv = x[i];
-        xv.x += ar * pv.x - ai * pv.y;
-        xv.y += ar * pv.y + ai * pv.x;
-        x[i] = xv;
-        rn[i] = make_double2(rv.x - (ar * qv.x - ai * qv.y), rv.y - (ar * qv.y + ai * qv.x));
-    }
-}
-
-__global__ void k_fcg_p(double2 *p, const double2 *z, size_t n, double br, double bi)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double2 pv = p[i], zv = z[i];
-        p[i] = make_double2(zv.x + br * pv.x - bi * pv.y, zv.y + br * pv.y + bi * pv.x);
-    }
-}
-
-// the dot products of one flexible-CG step in one pass (FIN_STORE values): 0 |rn|^2,
-// 1 + 2i <rn - r, z>, 3 + 4i <rn, z>, with <a, b> = sum conj(a) b
-__global__ void k_fcg_dots(const double2 *rn, const double2 *r, const double2 *z, size_t n, Reduce red)
-{
-    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double2 a = rn[i], b = r[i], c = z[i];
-        const double dx = a.x - b.x, dy = a.y - b.y;
-        v[0] += a.x * a.x + a.y * a.y;
-        v[1] += dx * c.x + dy * c.y;
-        v[2] += dx * c.y - dy * c.x;
-        v[3] += a.x * c.x + a.y * c.y;
-        v[4] += a.x * c.y - a.y * c.x;
-    }
-    block_sum_multi<5>(v);
-    grid_reduce<5>(red, v, 5, 0, 5, blockIdx.x);
-}
-
-__global__ void k_sub(const double2 *a, const double2 *b, double2 *c, size_t n)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        c[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
-}
-
 }  // namespace hisq
 
 using namespace hisq;
@@ -162,7 +117,7 @@ void hisq_net_opts_default(hisq_net_opts *o)
     std::memset(o, 0, sizeof(*o));
     o->nlayer = 4;
     o->channels = 8;
-    o->link_prec = HISQ_F32;
+    o->link_prec = HISQ_F16;
     o->epochs = 4;
     o->batch = 8;
     o->lr = 2e-3;
@@ -171,6 +126,7 @@ void hisq_net_opts_default(hisq_net_opts *o)
     o->eps = 1e-8;
     o->init_hop = 0.05;
     o->seed = 12345;
+    o->tensor_cores = 1;
 }
 
 int hisq_net_create(hisq_ctx *ctx, const hisq_net_opts *opts_in, hisq_net **out)
@@ -193,6 +149,8 @@ int hisq_net_create(hisq_ctx *ctx, const hisq_net_opts *opts_in, hisq_net **out)
     hisq_net *n = new hisq_net();
     n->ctx = ctx;
     n->device = ctx->device;
+    static std::atomic<unsigned long long> next_uid{1};
+    n->uid = next_uid++;
     n->opts = o;
     n->nlayer = o.nlayer;
     n->link_prec = o.link_prec;
@@ -297,7 +255,7 @@ int hisq_net_loss_grad(hisq_net *n, const double *b, const double *x, double *lo
     if ((rc = read_sc(n, st))) return rc;
     if (loss) *loss = n->h_sc[0].last / n->h_sc[1].last;
     if (grad) HISQ_CUDA(n->ctx, cudaMemcpy(grad, n->grad, sizeof(double2) * n->nw, cudaMemcpyDeviceToHost));
-    return HISQ_OK;
+    return check_device_status(n->ctx, st);
 }
 
 int hisq_net_train(hisq_net *n, int npairs, const double *B, const double *X, double *losses)
@@ -354,7 +312,7 @@ int hisq_net_train(hisq_net *n, int npairs, const double *B, const double *X, do
         if (losses) losses[ep] = acc / npairs;
     }
     HISQ_CUDA(ctx, cudaStreamSynchronize(st));
-    return HISQ_OK;
+    return check_device_status(ctx, st);
 }
 
 int hisq_net_save(const hisq_net *n, const char *path)
@@ -402,177 +360,6 @@ int hisq_net_load(hisq_ctx *ctx, const char *path, hisq_net **out)
         return set_error(ctx, HISQ_EINVAL, "hisq_net_load: weight count mismatch");
     }
     return hisq_net_set_weights(*out, w.data());
-}
-
-int hisq_fcg(hisq_ctx *ctx, double m, hisq_net *net, const double *b, double *x, const hisq_solve_opts *opts,
-             hisq_stats *stats)
-{
-    if (!ctx) return HISQ_EINVAL;
-    if (!b || !x || !(m >= 0.0) || (net && net->ctx != ctx)) return set_error(ctx, HISQ_EINVAL, "hisq_fcg: bad argument");
-    hisq_solve_opts o;
-    if (opts) o = *opts;
-    else hisq_solve_opts_default(&o);
-    const int pa = o.prec_precise == HISQ_F64X ? HISQ_F64X : HISQ_F64;
-    if (!ctx->links[pa].built || !ctx->links[HISQ_F64].built) return set_error(ctx, HISQ_ENOTBUILT, "hisq_fcg: precision");
-    if (stats) std::memset(stats, 0, sizeof(*stats));
-    cudaSetDevice(ctx->device);
-    const auto t0 = std::chrono::steady_clock::now();
-    const uint32_t Vh = ctx->g.Vh;
-    const size_t nc = (size_t)Vh * 3; // complex entries
-    const size_t vb = nc * 16, pb = (size_t)ctx->g.VhPad * 48;
-    // workspace: r, rn, z, p, q, t(odd), and float-pair copies for the F64X operator
-    std::vector<void *> mem;
-    auto A = [&](size_t bytes) -> char * {
-        void *p = nullptr;
-        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
-        cudaMemset(p, 0, bytes);
-        mem.push_back(p);
-        return static_cast<char *>(p);
-    };
-    auto release = [&]() {
-        for (void *p : mem) cudaFree(p);
-    };
-    char *r = A(vb), *rn = A(vb), *z = A(vb), *p = A(vb), *q = A(vb), *t = A(vb);
-    char *xx = A(pb), *tx = A(pb), *Ax = A(pb);
-    double *partials = (double *)A(sizeof(double) * 8 * 4096);
-    unsigned *counter = (unsigned *)A(64);
-    Scalars *sc = (Scalars *)A(sizeof(Scalars) * 8);
-    if (!r || !rn || !z || !p || !q || !t || !xx || !tx || !Ax || !partials || !counter || !sc) {
-        release();
-        return set_error(ctx, HISQ_ENOMEM, "hisq_fcg: workspace");
-    }
-    Scalars hsc[8];
-    cudaStream_t st = (cudaStream_t)o.stream;
-    const int nblk = (int)std::min<size_t>((Vh + kVecBlock - 1) / kVecBlock, 4ull * ctx->sm_count);
-    Reduce R;
-    R.partials = partials;
-    R.counter = counter;
-    R.sc = sc;
-    R.nblocks = nblk;
-    R.ntotal = nblk;
-    auto dot = [&](const char *a, const char *c, double &re, double &im) -> int {
-        Reduce Q = R;
-        Q.op = FIN_CDOT;
-        k_cdot<HISQ_F64><<<nblk, kVecBlock, 0, st>>>(VecRef{(char *)a, 0}, VecRef{(char *)c, 0}, Vh, Q);
-        if (cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return cuda_error(ctx, cudaGetLastError(), "hisq_fcg: reduction");
-        re = hsc[0].last;
-        im = hsc[0].last_im;
-        return HISQ_OK;
-    };
-    auto applyA = [&](int prec, const char *in, char *out) -> int {
-        if (prec == HISQ_F64) return apply_mdagm(ctx, HISQ_F64, m, in, t, out, 1, nc * 16, st, nullptr, true);
-        k_convert<HISQ_F64, HISQ_F64X><<<nblk, kVecBlock, 0, st>>>(VecRef{(char *)in, 0}, VecRef{xx, 0}, Vh);
-        int rc = apply_mdagm(ctx, HISQ_F64X, m, xx, tx, Ax, 1, pb, st, nullptr, true);
-        if (rc) return rc;
-        k_convert<HISQ_F64X, HISQ_F64><<<nblk, kVecBlock, 0, st>>>(VecRef{Ax, 0}, VecRef{out, 0}, Vh);
-        return HISQ_OK;
-    };
-    const int gb = (int)std::min<size_t>((nc + 255) / 256, 8ull * ctx->sm_count);
-    bool use_net = net != nullptr;
-    int fallbacks = 0;
-    // z = K(in) (identity once the network is dropped); a non-finite network output is
-    // caught by the dot products that follow
-    auto precond = [&](const char *in, char *out) -> int {
-        if (use_net) return net_forward(net, (const double *)in, (double *)out, st);
-        return cudaMemcpyAsync(out, in, vb, cudaMemcpyDeviceToDevice, st) == cudaSuccess ? HISQ_OK
-                                                                                            : cuda_error(ctx, cudaErrorUnknown, "copy");
-    };
-    auto step_dots = [&](const char *a, const char *c, const char *zz, double (&v)[5]) -> int {
-        Reduce Q = R;
-        Q.op = FIN_STORE;
-        k_fcg_dots<<<nblk, kVecBlock, 0, st>>>((const double2 *)a, (const double2 *)c, (const double2 *)zz, nc, Q);
-        if (cudaMemcpyAsync(hsc, sc, sizeof(Scalars) * 5, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return cuda_error(ctx, cudaGetLastError(), "hisq_fcg: reduction");
-        for (int i = 0; i < 5; i++) v[i] = hsc[i].last;
-        return HISQ_OK;
-    };
-    auto all_finite = [](const double (&v)[5]) {
-        for (double a : v)
-            if (!std::isfinite(a)) return false;
-        return true;
-    };
-    int rc = HISQ_OK;
-    double bb, tmp;
-    if (o.zero_guess) cudaMemsetAsync(x, 0, vb, st);
-    if ((rc = dot((const char *)b, (const char *)b, bb, tmp))) { release(); return rc; }
-    // r = b - A x
-    if ((rc = applyA(pa, (const char *)x, q))) { release(); return rc; }
-    k_sub<<<gb, 256, 0, st>>>((const double2 *)b, (const double2 *)q, (double2 *)r, nc);
-    if ((rc = precond(r, z))) { release(); return rc; }
-    double rz_re, rz_im, rr;
-    if ((rc = dot(r, z, rz_re, rz_im)) || (rc = dot(r, r, rr, tmp))) { release(); return rc; }
-    if (use_net && !(std::isfinite(rz_re) && std::isfinite(rz_im))) { // network output not finite
-        use_net = false;
-        fallbacks++;
-        if ((rc = precond(r, z)) || (rc = dot(r, z, rz_re, rz_im))) { release(); return rc; }
-    }
-    cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, st);
-    int it = 0, since_best = 0;
-    double best = rr;
-    const double stop = o.tol * o.tol * bb;
-    bool converged = !(rr > stop);
-    while (!converged && it < o.maxiter) {
-        if ((rc = applyA(pa, p, q))) break;
-        double pq, pq_im;
-        if ((rc = dot(p, q, pq, pq_im))) break;
-        if (!(pq > 0.0)) { rc = HISQ_ENOTCONVERGED; break; }
-        // alpha = <r,z> / <p,Ap>
-        const double ar = rz_re / pq, ai = rz_im / pq;
-        k_fcg_update<<<gb, 256, 0, st>>>((double2 *)x, (const double2 *)p, (const double2 *)q, (const double2 *)r,
-                                         (double2 *)rn, nc, ar, ai);
-        it++;
-        // z' = K r'; |r'|^2, <r' - r, z'>, <r', z'> in one pass
-        if ((rc = precond(rn, z))) break;
-        double v[5];
-        if ((rc = step_dots(rn, r, z, v))) break;
-        if (use_net && !all_finite(v)) { // drop the network, continue with K = identity
-            use_net = false;
-            fallbacks++;
-            if ((rc = precond(rn, z)) || (rc = step_dots(rn, r, z, v))) break;
-        }
-        rr = v[0];
-        if (!std::isfinite(rr)) { rc = HISQ_ENOTCONVERGED; break; }
-        if (rr < best) { best = rr; since_best = 0; }
-        else if (++since_best >= 50 && use_net) { use_net = false; fallbacks++; since_best = 0; }
-        if (rr <= stop) {
-            // confirm with the FP64 operator
-            if ((rc = applyA(HISQ_F64, (const char *)x, q))) break;
-            k_sub<<<gb, 256, 0, st>>>((const double2 *)b, (const double2 *)q, (double2 *)rn, nc);
-            double rt;
-            if ((rc = dot(rn, rn, rt, tmp))) break;
-            if (rt <= stop) { rr = rt; converged = true; break; }
-            rr = rt; // restart from the true residual
-            std::swap(r, rn);
-            if ((rc = precond(r, z))) break;
-            cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, st);
-            if ((rc = dot(r, z, rz_re, rz_im))) break;
-            continue;
-        }
-        // beta = <r' - r, z'> / <r, z>  (Polak-Ribiere)
-        const double nr = v[1], ni = v[2];
-        const double den = rz_re * rz_re + rz_im * rz_im;
-        const double br = (nr * rz_re + ni * rz_im) / den, bi = (ni * rz_re - nr * rz_im) / den;
-        k_fcg_p<<<gb, 256, 0, st>>>((double2 *)p, (const double2 *)z, nc, br, bi);
-        std::swap(r, rn);
-        rz_re = v[3];
-        rz_im = v[4];
-    }
-    cudaStreamSynchronize(st);
-    release();
-    if (stats) {
-        stats->iterations = it;
-        stats->reliable_updates = fallbacks;
-        stats->true_residual = std::sqrt(rr / bb);
-        stats->iterated_residual = std::sqrt(rr / bb);
-        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        stats->dslash_calls = 2L * (it + 2);
-    }
-    if (rc && rc != HISQ_ENOTCONVERGED) return rc;
-    if (!converged) return set_error(ctx, HISQ_ENOTCONVERGED, "hisq_fcg: tolerance not reached");
-    return HISQ_OK;
 }
 
 }  // extern "C"

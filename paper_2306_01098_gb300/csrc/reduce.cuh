@@ -45,6 +45,11 @@ enum FinishOp {
     FIN_ALPHA = 1, // pAp = total; alpha = rr / pAp
     FIN_RR = 2,    // beta = total / rr; rr = total; set flag when below stop / delta
     FIN_CDOT = 3,  // value 2k -> last, 2k+1 -> last_im of right-hand side k
+    FIN_AB = 4,    // values 4k .. 4k+3 = <p,Ap>, |r|^2, <r,Ap>, <Ap,Ap> of right-hand side k:
+                   // alpha = |r|^2 / <p,Ap> (curvature checked as FIN_ALPHA), then
+                   // |r - alpha Ap|^2 = |r|^2 - 2 alpha <r,Ap> + alpha^2 <Ap,Ap> and
+                   // everything FIN_RR does with it.  |r|^2 is reduced afresh from the stored
+                   // r each iteration, so the rounding of the expansion does not accumulate.
 };
 
 // iteration control of a device-side solver loop (a CUDA graph WHILE node): the block that
@@ -69,8 +74,32 @@ struct Reduce {
 
 __device__ __forceinline__ void finish_value(const Reduce &R, int v, double total)
 {
-    Scalars &S = R.sc[R.op == FIN_CDOT ? (v >> 1) : v];
-    switch (R.op) {
+    Scalars &S = R.sc[R.op == FIN_CDOT ? (v >> 1) : R.op == FIN_AB ? (v >> 2) : v];
+    int op = R.op;
+    if (op == FIN_AB) {
+        switch (v & 3) {
+        case 0: S.pAp = total; return;     // <p, Ap>
+        case 1: S.last_im = total; return; // |r|^2 of the stored r
+        case 2: S.last = total; return;    // <r, Ap>
+        default: break;                    // <Ap, Ap>: finish
+        }
+        if (S.active && isfinite(S.last_im)) S.rr = S.last_im;
+        const double pAp = S.pAp;
+        S.astamp = S.it_all;
+        if (S.active && !(pAp > 0.0 && isfinite(pAp))) {
+            S.bad = 1;
+            S.active = 0;
+        }
+        S.alpha = S.active ? S.rr / pAp : 0.0;
+        double rr = S.rr;
+        if (S.active) {
+            rr = S.rr - 2.0 * S.alpha * S.last + S.alpha * S.alpha * total;
+            if (isfinite(rr) && rr < 0.0) rr = 0.0; // rounding: the residual has vanished
+        }
+        total = rr;
+        op = FIN_RR;
+    }
+    switch (op) {
     case FIN_ALPHA:
         S.pAp = total;
         S.astamp = S.it_all;
@@ -133,12 +162,12 @@ __device__ __forceinline__ double block_sum(double x)
     return r;
 }
 
-// loop control after the final sums (thread 0)
-__device__ __forceinline__ void finish_control(const Reduce &R, int nval_all)
+// loop control after the final sums (thread 0); nrhs = right-hand sides (scalars)
+__device__ __forceinline__ void finish_control(const Reduce &R, int nrhs)
 {
     if (R.ctl) {
         bool any = false;
-        for (int v = 0; v < nval_all; v++) any |= R.sc[v].active != 0;
+        for (int v = 0; v < nrhs; v++) any |= R.sc[v].active != 0;
         const bool last = R.sc[0].it_all - R.ctl->start >= R.ctl->cap;
         R.ctl->mode = last ? 1 : 0;
         if (R.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)R.cond, (any && !last) ? 1u : 0u);
@@ -203,7 +232,7 @@ __device__ __forceinline__ void grid_reduce(const Reduce &R, const double (&mine
         if (threadIdx.x == 0) finish_value(R, v, x);
     }
     if (threadIdx.x == 0) {
-        finish_control(R, nval_all);
+        finish_control(R, R.op == FIN_AB ? nval_all / 4 : R.op == FIN_CDOT ? nval_all / 2 : nval_all);
         __threadfence();
         *R.counter = 0u;
     }

@@ -30,6 +30,7 @@ struct SolverWork {
     cudaGraphExec_t graph = nullptr;
     double graph_m = -1.0;
     bool graph_l2 = false;
+    bool fused = true, graph_fused = true; // single-reduction iteration (this call, the captured graph)
     std::vector<cudaEvent_t> prof;
     std::vector<void *> allocs;
 

@@ -161,3 +161,21 @@ def test_uneven_32_lattice_batch():
         r = bs[k].cpu().numpy() - oracle.mdagm(dims[k], fat.numpy(), lng.numpy(), 0.1, xk)
         assert np.linalg.norm(r) / np.linalg.norm(bs[k].cpu().numpy()) <= 1e-10
     batch.close()
+
+
+def test_batch_cg_single_reduction_matches_two_reduction(small_batch):
+    # the single-reduction iteration over a batch of uneven lattices (three epilogue values per
+    # lattice, zero partials beyond each lattice's own tiles) against the two-reduction form
+    members, batch = small_batch
+    n = len(members)
+    _, bp = packed(members, 2500)
+    bp = bp.cuda()
+    its = {}
+    for single in (1, 0):
+        x = torch.zeros_like(bp)
+        res = torch.zeros(n, dtype=torch.float64)
+        rc, st = batch.cg([0.1] * n, bp, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64,
+                          single_reduction=single, residuals=res)
+        assert rc == hisq.OK and float(res.max()) <= 1e-10
+        its[single] = st.iterations
+    assert abs(its[1] - its[0]) <= 3

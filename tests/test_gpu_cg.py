@@ -190,3 +190,29 @@ def test_cg_many_reduction_chunks(ds):
     for r in range(nrhs):
         assert true_res(dims, fat, lng, m, b[r].numpy(), xg[r]) <= 1e-10
     ctx.close()
+
+
+@pytest.mark.parametrize("sloppy,nrhs", [(hisq.F64, 1), (hisq.F32, 1), (hisq.F16, 1), (hisq.F32, 4), (hisq.F16, 3)])
+def test_single_and_two_reduction_iterations_agree(sloppy, nrhs):
+    # the single-reduction iteration (|r'|^2 from <r,Ap> and <Ap,Ap> in the operator's
+    # epilogue) and the two-reduction form solve the same systems to the FP64 tolerance in
+    # about the same number of iterations; in FP64 the iterates are the same to rounding
+    dims, m = (8, 8, 8, 12), 0.02
+    ctx, fat, lng = setup(dims, 0.5, 1001)
+    b = fields.gaussian_source(dims, 2150, nrhs)
+    out = {}
+    for single in (1, 0):
+        x = torch.zeros_like(b).cuda()
+        res = torch.zeros(nrhs, dtype=torch.float64)
+        rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=sloppy, prec_precise=hisq.F64, reliable_delta=0.01,
+                        single_reduction=single, residuals=res)
+        assert rc == hisq.OK
+        for k in range(nrhs):
+            assert true_res(dims, fat, lng, m, b[k].numpy(), x[k].cpu().numpy()) <= 1e-10
+        out[single] = (st.iterations, x.cpu().numpy())
+    its1, its0 = out[1][0], out[0][0]
+    print(f"sloppy {sloppy} nrhs {nrhs}: single-reduction {its1} iterations, two-reduction {its0}")
+    assert abs(its1 - its0) <= max(2, 0.05 * its0)
+    if sloppy == hisq.F64:
+        xa, xb = out[1][1], out[0][1]
+        assert np.linalg.norm(xa - xb) <= 1e-9 * np.linalg.norm(xb)

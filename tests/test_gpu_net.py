@@ -43,10 +43,11 @@ def small():
     return dims, ctx, fat.numpy(), lng.numpy()
 
 
+@pytest.mark.parametrize("tensor_cores", [1, 0])
 @pytest.mark.parametrize("link_prec,tol", [(hisq.F32, 3e-2), (hisq.F16, 3e-2)])
-def test_network_forward_matches_oracle(small, link_prec, tol):
+def test_network_forward_matches_oracle(small, link_prec, tol, tensor_cores):
     dims, ctx, fat, lng = small
-    net = hisq.Net(ctx, link_prec=link_prec)
+    net = hisq.Net(ctx, link_prec=link_prec, tensor_cores=tensor_cores)
     chans = [1, 8, 8, 8, 1]
     w = rand_weights(chans, 5)
     assert w.size == net.nw
@@ -56,6 +57,34 @@ def test_network_forward_matches_oracle(small, link_prec, tol):
     net.apply(b.cuda(), z)
     want = oracle.net_apply(dims, fat, lng, chans, w, b.numpy())
     assert rel(z.cpu().numpy(), want) <= tol
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8, 10), (6, 6, 4, 10)])
+def test_tensor_core_layers_match_cuda_core_layers(dims):
+    # the 8 -> 8 layers' channel mixing on the tensor cores (BF16 operands, FP32 accumulation)
+    # against the same network in FP32 on the CUDA cores: 128-site tiles, a ragged last tile
+    # (V = 5120 = 40 tiles; V = 1440 = 11.25 tiles), identical weights, and the oracle
+    fat, lng = fields.recipe_links(dims, 0.5, 79)
+    ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=(hisq.F64, hisq.F32, hisq.F16))
+    chans = [1, 8, 8, 8, 1]
+    w = rand_weights(chans, 11)
+    nets = [hisq.Net(ctx, tensor_cores=t) for t in (1, 0)]
+    b = fields.gaussian_source(dims, 330)[0]
+    outs = []
+    for net in nets:
+        net.set_weights(w)
+        z = torch.empty_like(b).cuda()
+        net.apply(b.cuda(), z)
+        outs.append(z.cpu().numpy())
+    want = oracle.net_apply(dims, fat.numpy(), lng.numpy(), chans, w, b.numpy())
+    assert rel(outs[1], want) <= 3e-2
+    assert rel(outs[0], want) <= 3e-2
+    assert rel(outs[0], outs[1]) <= 3e-2
+    # every site was written: no site of the tensor-core output is left at zero
+    assert np.abs(outs[0]).reshape(-1, 6).max(axis=1).min() > 0.0
+    for net in nets:
+        net.close()
+    ctx.close()
 
 
 def test_network_loss_and_gradient_match_oracle(small):
@@ -174,7 +203,7 @@ def test_network_may_outlive_its_context():
     dims = (6, 4, 4, 6)
     fat, lng = fields.recipe_links(dims, 0.5, 78)
     ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=(hisq.F64, hisq.F32))
-    net = hisq.Net(ctx)
+    net = hisq.Net(ctx, link_prec=hisq.F32)
     ctx.close()
     net.close()
     torch.cuda.synchronize()
