@@ -283,6 +283,11 @@ typedef struct {
     int tensor_cores;      /* 1 (default): the channel mixing of the 8 -> 8 layers runs on the
                               tensor cores (tcgen05, BF16 operands, FP32 accumulation in
                               tensor memory); 0: FP32 arithmetic on the CUDA cores            */
+    int selftest_wait;     /* testing only (default 0): every tensor-core layer launch first
+                              waits, for about 1 ms, on a barrier that nothing completes, so
+                              that the bounded-wait error path runs: the layer's output is not
+                              written and the next synchronising call (loss/gradient, train,
+                              flexible CG) returns HISQ_EDEVICE                              */
 } hisq_net_opts;
 
 void hisq_net_opts_default(hisq_net_opts *opts);

@@ -64,6 +64,7 @@ struct NetLayerArgs {
     int even_only_in;    // input lives on even sites only (odd sites read as zero)
     int even_only_out;   // compute the even output sites only (the odd ones are not written)
     int tensor_cores;    // C -> C layers with C = 8 mix channels on the tensor cores
+    int selftest_wait;   // first wait (bounded) on a barrier that nothing completes
     DevStatus *status;   // device error flag (bounded waits of the tensor-core layer)
 };
 
@@ -237,6 +238,7 @@ struct NetTcSmem {
     alignas(1024) uint8_t A[2][3][kTcTile];  // two stages x three colours
     alignas(128) uint8_t B[kNetTaps][512];   // per tap: 16 x 16 BF16, K-major
     uint64_t bar[2];
+    uint64_t probe;                          // completed by nothing (self-test of the wait path)
     uint32_t tmem;
 };
 
@@ -302,6 +304,7 @@ __global__ void __launch_bounds__(128, 5) k_net_layer_tc(const NetLayerArgs a, D
     if (r == 0) {
         tc::mbar_init(&sm.bar[0], 1);
         tc::mbar_init(&sm.bar[1], 1);
+        tc::mbar_init(&sm.probe, 1);
         tc::mbar_fence_init();
     }
     tc::fence_before_sync();
@@ -309,12 +312,14 @@ __global__ void __launch_bounds__(128, 5) k_net_layer_tc(const NetLayerArgs a, D
     tc::fence_after_sync();
     const uint32_t tmem = sm.tmem;
     constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcRows, 2 * C);
+    bool ok = true;
+    // self-test: a bounded wait that runs out (nothing arrives on the probe barrier)
+    if (a.selftest_wait) ok &= tc::mbar_wait(&sm.probe, 0, 1000000ull);
 
     // tiles alternate between the parities over the same half-sites (links reused in L2)
     const uint32_t tpp = (a.g.Vh + kTcRows - 1) / kTcRows; // tiles per parity
     const uint32_t ntiles = a.even_only_out ? tpp : 2 * tpp;
     uint32_t issued0 = 0u, issued1 = 0u; // commits on each stage so far (the same in every thread)
-    bool ok = true;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int p = a.even_only_out ? 0 : (int)(tile & 1);
         const uint32_t s0 = (a.even_only_out ? tile : tile >> 1) * kTcRows + r;
@@ -712,6 +717,7 @@ static NetLayerArgs layer_args(const hisq_net *n, const float2 *w, const uint32_
     a.even_only_in = even_in;
     a.even_only_out = even_out;
     a.tensor_cores = n->opts.tensor_cores;
+    a.selftest_wait = n->opts.selftest_wait;
     a.status = n->ctx->status;
     return a;
 }

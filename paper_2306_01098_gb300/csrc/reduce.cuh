@@ -219,17 +219,28 @@ __device__ __forceinline__ void grid_reduce(const Reduce &R, const double (&mine
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int v = 0; v < nval_all; v++) {
-        const double *pv = R.partials + (size_t)v * R.nblocks;
-        double x = 0.0;
-        for (int i0 = threadIdx.x; i0 < R.nblocks; i0 += 4 * blockDim.x) {
-            double t[4];
+    // NV values at a time through one block-wide reduction (the same summation order as one
+    // value at a time, fewer barriers in this serial tail); finished in value order
+    for (int v0 = 0; v0 < nval_all; v0 += NV) {
+        double x[NV];
 #pragma unroll
-            for (int u = 0; u < 4; u++) t[u] = i0 + u * (int)blockDim.x < R.nblocks ? __ldcg(pv + i0 + u * blockDim.x) : 0.0;
-            x += (t[0] + t[1]) + (t[2] + t[3]);
+        for (int k = 0; k < NV; k++) {
+            double acc = 0.0;
+            if (v0 + k < nval_all) {
+                const double *pv = R.partials + (size_t)(v0 + k) * R.nblocks;
+                for (int i0 = threadIdx.x; i0 < R.nblocks; i0 += 4 * blockDim.x) {
+                    double t[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        t[u] = i0 + u * (int)blockDim.x < R.nblocks ? __ldcg(pv + i0 + u * blockDim.x) : 0.0;
+                    acc += (t[0] + t[1]) + (t[2] + t[3]);
+                }
+            }
+            x[k] = acc;
         }
-        x = block_sum(x);
-        if (threadIdx.x == 0) finish_value(R, v, x);
+        block_sum_multi<NV>(x);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < NV && v0 + k < nval_all; k++) finish_value(R, v0 + k, x[k]);
     }
     if (threadIdx.x == 0) {
         finish_control(R, R.op == FIN_AB ? nval_all / 4 : R.op == FIN_CDOT ? nval_all / 2 : nval_all);

@@ -59,7 +59,7 @@ class NetOpts(ctypes.Structure):
                 ("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
                 ("init_hop", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("loss", ctypes.c_int),
-                ("mass", ctypes.c_double), ("tensor_cores", ctypes.c_int)]
+                ("mass", ctypes.c_double), ("tensor_cores", ctypes.c_int), ("selftest_wait", ctypes.c_int)]
 
 
 _P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long

@@ -216,3 +216,20 @@ def test_single_and_two_reduction_iterations_agree(sloppy, nrhs):
     if sloppy == hisq.F64:
         xa, xb = out[1][1], out[0][1]
         assert np.linalg.norm(xa - xb) <= 1e-9 * np.linalg.norm(xb)
+
+
+@pytest.mark.parametrize("single", [1, 0])
+def test_pause_inside_timed_iterations_ends_device_loop(single):
+    # with profile = 1 the first two iterations of a phase are launched directly and timed;
+    # a large reliable-update delta pauses the right-hand side inside them, so the device loop
+    # that follows starts with nothing active: it must end at once (the idle launch still runs
+    # the loop control) and must not apply the last alpha a second time
+    dims, m = (8, 8, 8, 12), 0.02
+    ctx, fat, lng = setup(dims, 0.5, 1001)
+    b = fields.gaussian_source(dims, 2170)[0]
+    x = torch.zeros_like(b).cuda()
+    rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, reliable_delta=0.5,
+                    profile=1, single_reduction=single)
+    assert rc == hisq.OK
+    assert true_res(dims, fat, lng, m, b.numpy(), x.cpu().numpy()) <= 1e-10
+    print(f"single_reduction {single}: {st.iterations} iterations, {st.reliable_updates} reliable updates")

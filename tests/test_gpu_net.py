@@ -208,3 +208,29 @@ def test_network_may_outlive_its_context():
     net.close()
     torch.cuda.synchronize()
     assert float(torch.ones(4, device="cuda").sum()) == 4.0
+
+
+def test_bounded_wait_error_reaches_the_host():
+    # the tensor-core layer's barrier waits are bounded: with the self-test option every layer
+    # launch first waits on a barrier that nothing completes; the wait runs out (about 1 ms),
+    # the kernel raises the context's device error flag and skips its output, and the next
+    # synchronising call returns HISQ_EDEVICE.  The context stays usable afterwards.
+    dims = (6, 4, 4, 6)
+    fat, lng = fields.recipe_links(dims, 0.5, 80)
+    ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=(hisq.F64, hisq.F32, hisq.F16))
+    net = hisq.Net(ctx, selftest_wait=1)
+    b = fields.gaussian_source(dims, 340)[0].cuda()
+    x = fields.gaussian_source(dims, 341)[0].cuda()
+    with pytest.raises(hisq.HisqError) as err:
+        net.loss_grad(b, x)
+    assert err.value.code == hisq.EDEVICE
+    net.close()
+    # the same context still computes correct results
+    out = torch.empty_like(b)
+    ctx.dslash(0, b, out)
+    want = oracle.dslash(dims, fat.numpy(), lng.numpy(), b.cpu().numpy(), 0)
+    assert np.abs(out.cpu().numpy() - want).max() <= 1e-13 * np.abs(want).max()
+    good = hisq.Net(ctx)
+    good.loss_grad(b, x)
+    good.close()
+    ctx.close()
