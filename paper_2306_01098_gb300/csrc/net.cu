@@ -293,7 +293,9 @@ __global__ void __launch_bounds__(128, 5) k_net_layer_tc(const NetLayerArgs a, D
     // B tiles from the complex weights w[tap][c'][c]: rows n = 2c' + (0 re, 1 im), k = 2c + (0 re, 1 im)
     for (int q = r; q < kNetTaps * C * C; q += blockDim.x) {
         const int tap = q / (C * C), o = (q / C) % C, ci = q % C;
-        const float2 w = a.w[q];
+        // the links' per-type storage scale is folded into the weights of their taps
+        const float ls = tap == 0 ? 1.f : a.scale[tap >= 9 ? 1 : 0];
+        const float2 w = make_float2(a.w[q].x * ls, a.w[q].y * ls);
         uint8_t *bt = sm.B[tap];
         *reinterpret_cast<__nv_bfloat16 *>(bt + tc_off(2 * o, 2 * ci)) = __float2bfloat16_rn(w.x);
         *reinterpret_cast<__nv_bfloat16 *>(bt + tc_off(2 * o, 2 * ci + 1)) = __float2bfloat16_rn(-w.y);
@@ -338,13 +340,10 @@ __global__ void __launch_bounds__(128, 5) k_net_layer_tc(const NetLayerArgs a, D
             uint32_t row[3][C]; // colour, channel: BF16 pair (re, im) of the transported input
             if (live) {
                 if (tap > 0) {
-                    const int k = tap - 1, type = k >= 8, back = k & 1;
+                    // the stored link; its per-type scale is folded into the B tile
+                    const int back = (tap - 1) & 1;
                     typename Prec<HISQ_F32>::Link U;
                     Prec<PL>::template unpack<18>(L.lw, U);
-                    if constexpr (PL == HISQ_F16 || PL == HISQ_BF16) {
-#pragma unroll
-                        for (int q = 0; q < 18; q++) U.v[q] *= type ? a.scale[1] : a.scale[0];
-                    }
 #pragma unroll
                     for (int ch = 0; ch < C; ch++) {
                         float v[6], t[6];
