@@ -233,3 +233,29 @@ def test_pause_inside_timed_iterations_ends_device_loop(single):
     assert rc == hisq.OK
     assert true_res(dims, fat, lng, m, b.numpy(), x.cpu().numpy()) <= 1e-10
     print(f"single_reduction {single}: {st.iterations} iterations, {st.reliable_updates} reliable updates")
+
+
+def test_bench_configuration_full_size():
+    # the benchmark's solve at its full size and launch configuration (32^3 x 8, eps 0.5,
+    # m 0.01, 16-bit links with FP32 vectors, FP64 reliable updates, delta 0.01, timed phases,
+    # graph loop): the oracle recomputes |b - A x| / |b| in FP64, and the mixed-precision x
+    # agrees with the GPU's plain FP64 solve within kappa(A) tol
+    from hisq_inputs import workloads
+    w = workloads.MIXED_32x8
+    fat, lng = fields.recipe_links(w.dims, w.eps, w.link_seed)
+    ctx = hisq.Context(w.dims, fat.cuda(), lng.cuda(), precs=(hisq.F64, hisq.F16))
+    b = fields.gaussian_source(w.dims, w.source_seed)[0]
+    x = torch.zeros_like(b).cuda()
+    rc, st = ctx.cg(w.mass, b.cuda(), x, tol=w.tol, prec_sloppy=hisq.F16, prec_precise=hisq.F64, reliable_delta=0.01,
+                    profile=1, use_graph=1)
+    assert rc == hisq.OK
+    res = true_res(w.dims, fat.numpy(), lng.numpy(), w.mass, b.numpy(), x.cpu().numpy())
+    assert res <= 1e-10
+    x64 = torch.zeros_like(b).cuda()
+    rc, st64 = ctx.cg(w.mass, b.cuda(), x64, tol=w.tol, prec_sloppy=hisq.F64)
+    assert rc == hisq.OK
+    rel = float((x - x64).norm() / x64.norm())
+    kappa = (4 * (w.mass ** 2 + 4 * (1 + 1 / 24) ** 2)) / (4 * w.mass ** 2)
+    print(f"bench configuration: {st.iterations} iterations, true residual {res:.2e}, |x - x64|/|x64| {rel:.2e}")
+    assert rel <= kappa * 1e-10
+    ctx.close()
