@@ -125,7 +125,7 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b)
 // set-up scalars after r and z: rz = <r, z>, rr = |r|^2 (values 0, 1 + 2i of the partials)
 __global__ void __launch_bounds__(kVecBlock) k_fcg_start(const double2 *r, const double2 *z, size_t n,
                                                           double *partials, unsigned *counter, FcgScalars *sc,
-                                                          double tol2, int stagnation_check)
+                                                          int stagnation_check)
 {
     double v[3] = {0.0, 0.0, 0.0};
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -143,7 +143,6 @@ __global__ void __launch_bounds__(kVecBlock) k_fcg_start(const double2 *r, const
         S.stagnation_check = stagnation_check;
         S.state = (isfinite(t[0]) && isfinite(t[1]) && isfinite(t[2])) ? FCG_RUN : FCG_NONFINITE;
         if (S.state == FCG_RUN && t[0] <= S.stop) S.state = FCG_CONVERGED;
-        (void)tol2;
     });
 }
 
@@ -444,7 +443,7 @@ static int read_fcg(hisq_ctx *ctx, FcgWork &w)
 }
 
 // r = b - A x (operator pa), z = K r, p = z, rz, rr: the start of a solve or a restart
-static int fcg_restart(hisq_ctx *ctx, FcgWork &w, hisq_net *net, bool use_net, int pa, double m, double tol2)
+static int fcg_restart(hisq_ctx *ctx, FcgWork &w, hisq_net *net, bool use_net, int pa, double m)
 {
     const size_t n = (size_t)w.Vh * 3;
     int rc = fcg_apply(ctx, w, pa, m, w.x, true);
@@ -455,7 +454,7 @@ static int fcg_restart(hisq_ctx *ctx, FcgWork &w, hisq_net *net, bool use_net, i
     // z = K r: the copy kernel reads the state, so mark the solve running first
     HISQ_CUDA(ctx, cudaMemsetAsync(&w.sc->state, 0, sizeof(int), w.st));
     if ((rc = fcg_precond(net, w, use_net))) return rc;
-    k_fcg_start<<<w.nblk, kVecBlock, 0, w.st>>>(w.r, w.z, n, w.partials, w.counter, w.sc, tol2, use_net ? 1 : 0);
+    k_fcg_start<<<w.nblk, kVecBlock, 0, w.st>>>(w.r, w.z, n, w.partials, w.counter, w.sc, use_net ? 1 : 0);
     HISQ_CUDA(ctx, cudaMemcpyAsync(w.p, w.z, w.vb, cudaMemcpyDeviceToDevice, w.st));
     HISQ_CUDA(ctx, cudaGetLastError());
     return HISQ_OK;
@@ -499,12 +498,12 @@ extern "C" int hisq_fcg(hisq_ctx *ctx, double m, hisq_net *net, const double *b,
     bool use_net = net != nullptr;
     int fallbacks = 0, loops = 0, restarts = 0;
     long kernels = 0;
-    if ((rc = fcg_restart(ctx, w, net, use_net, pa, m, tol2))) goto done;
+    if ((rc = fcg_restart(ctx, w, net, use_net, pa, m))) goto done;
     if ((rc = read_fcg(ctx, w))) goto done;
     if (w.h_sc->state == FCG_NONFINITE && use_net) { // network output not finite: plain CG
         use_net = false;
         fallbacks++;
-        if ((rc = fcg_restart(ctx, w, net, false, pa, m, tol2)) || (rc = read_fcg(ctx, w))) goto done;
+        if ((rc = fcg_restart(ctx, w, net, false, pa, m)) || (rc = read_fcg(ctx, w))) goto done;
     }
     for (;;) {
         const FcgScalars &S = *w.h_sc;
@@ -517,14 +516,14 @@ extern "C" int hisq_fcg(hisq_ctx *ctx, double m, hisq_net *net, const double *b,
             // the iterated residual ran ahead of the true one: restart from the iterate with
             // the FP64 residual (so a restart cannot report convergence the FP64 check denies)
             if (++restarts > kMaxRestarts) { rc = HISQ_ENOTCONVERGED; break; }
-            if ((rc = fcg_restart(ctx, w, net, use_net, HISQ_F64, m, tol2)) || (rc = read_fcg(ctx, w))) break;
+            if ((rc = fcg_restart(ctx, w, net, use_net, HISQ_F64, m)) || (rc = read_fcg(ctx, w))) break;
             continue;
         }
         if (S.state == FCG_NONFINITE || S.state == FCG_STAGNATED) {
             if (!use_net) { rc = HISQ_ENOTCONVERGED; break; }
             use_net = false; // drop the network; continue as CG from the current iterate
             fallbacks++;
-            if ((rc = fcg_restart(ctx, w, net, false, pa, m, tol2)) || (rc = read_fcg(ctx, w))) break;
+            if ((rc = fcg_restart(ctx, w, net, false, pa, m)) || (rc = read_fcg(ctx, w))) break;
             continue;
         }
         if (S.state == FCG_CURVATURE) { rc = HISQ_ENOTCONVERGED; break; }
