@@ -21,7 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 __all__ = [
-    "build", "lib", "dslash", "dslash_site", "mdagm", "cg", "cg_fixed", "multishift_cg",
+    "build", "lib", "dslash", "dslash_site", "mdagm", "cg", "cg_fixed", "multishift_cg", "rational_apply",
     "phase_links", "eo_index", "coords", "count_site", "net_layer", "net_layer_backward",
     "net_apply", "net_loss_grad", "net_loss_grad_residual", "fcg", "fcg_dense", "dense_A", "dense_D", "NTAP",
     "set_threads",
@@ -196,6 +196,17 @@ def multishift_cg(dims, fat, lng, m, sigma, b, tol, maxiter=100000, phased=False
     lib().ho_multishift_cg(_ptr(d), _ptr(F), _ptr(W), int(phased), float(m), ns, _ptr(sig), _ptr(bb),
                            _ptr(x), _ptr(tols), int(maxiter), _ptr(st))
     return x, int(st[0]), st[1:].copy()
+
+
+def rational_apply(dims, fat, lng, m, alpha0, alpha, sigma, b, tol=1e-12, phased=False):
+    """r(A) b = alpha0 b + sum_s alpha_s (A + sigma_s)^-1 b with the (A + sigma_s)^-1 b of one
+    multi-shift CG solve (the way RHMC uses the solver, Sec. 3.2).  Returns (x, true residual
+    of every shifted system)."""
+    xs, _, res = multishift_cg(dims, fat, lng, m, sigma, b, tol, phased=phased)
+    out = alpha0 * np.asarray(b, dtype=np.complex128)
+    for a, x in zip(alpha, xs):
+        out = out + a * x
+    return out, res
 
 
 def net_layer(dims, fat, lng, w, inp, cin, cout, phased=False):

@@ -267,3 +267,27 @@ def test_multishift_vs_independent_cg_6x4():
         ms = math.sqrt(m * m + sg / 4)
         xs, _, _, rt = oracle.cg(dims, fat, lng, ms, b, tol=1e-11)
         assert np.linalg.norm(x[s] - xs) / np.linalg.norm(xs) < 1e-8
+
+
+def test_rational_apply_matches_dense_spectral_evaluation():
+    # r(A) b = alpha0 b + sum_s alpha_s (A + sigma_s)^-1 b from one multi-shift solve, against
+    # V r(Lambda) V^+ b with the dense eigendecomposition of A on 4^4 (a dropped coefficient,
+    # a shift applied with the wrong sign or to the wrong term fails it)
+    from hisq_inputs import rational
+    dims, m = (4, 4, 4, 4), 0.1
+    fat, lng = fields.recipe_links(dims, 0.3, 48)
+    fat, lng = fat.numpy(), lng.numpy()
+    b = fields.gaussian_source(dims, 96)[0].numpy()
+    A = oracle.dense_A(dims, fat, lng, m)
+    lam, V = np.linalg.eigh(A)
+    a0, al, sg = rational.inv_sqrt(24, 0.9 * lam[0], 1.1 * lam[-1])
+    a0 = 0.25  # exercise the constant term as well
+    x, res = oracle.rational_apply(dims, fat, lng, m, a0, al, sg, b, tol=1e-13)
+    assert res.max() <= 1e-12
+    r_lam = a0 + sum(a / (lam + s) for a, s in zip(al, sg))
+    want = V @ (r_lam * (V.conj().T @ b.reshape(-1)))
+    assert np.linalg.norm(x.reshape(-1) - want) <= 1e-11 * np.linalg.norm(want)
+    # and r approximates A^-1/2 to the quadrature's accuracy on this spectrum
+    exact = V @ ((lam ** -0.5) * (V.conj().T @ b.reshape(-1)))
+    err = np.linalg.norm((x.reshape(-1) - a0 * b.reshape(-1)) - exact) / np.linalg.norm(exact)
+    assert err <= 2e-3
