@@ -227,6 +227,19 @@ int hisq_multishift_cg(hisq_ctx *ctx, double m, int nshift, const double *sigma,
                        const double *b, double *const *x, const double *tol,
                        const hisq_solve_opts *opts, hisq_stats *stats, double *residuals);
 
+/* r(A) b = alpha0 b + sum_s alpha_s (A + sigma_s)^-1 b: a rational function of A applied to b
+ * from one multi-shift solve, the way RHMC's pseudofermion heat bath and force use the
+ * multi-shift inverter (Sec. 3.2 "Inverters"; the paper prints no coefficients, the caller
+ * supplies the partial fractions of its rational approximation).  nterm in 1..64, sigma_s >= 0
+ * and finite, alpha_s and alpha0 finite.  Every shifted system is solved to opts->tol (true
+ * relative residual, FP64) with opts' precisions; `residuals` (may be NULL) receives the nterm
+ * true residuals.  b, x: canonical complex128 [Vh][3] device buffers, no overlap.  The call
+ * allocates nterm solution vectors for its duration and synchronises before returning.
+ * Returns HISQ_ENOTCONVERGED (x still formed) if a shifted system missed the tolerance. */
+int hisq_rational_apply(hisq_ctx *ctx, double m, int nterm, const double *alpha, const double *sigma,
+                        double alpha0, const double *b, double *x, const hisq_solve_opts *opts,
+                        hisq_stats *stats, double *residuals);
+
 /* ------------------------------------------------------------------ batches of lattices */
 /* Several lattices of different sizes (each its own context, links and mass) in single
  * launches.  The paper runs one lattice at a time and has no counterpart; the Dslash of a

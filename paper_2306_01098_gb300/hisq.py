@@ -78,6 +78,8 @@ _SIGS = {
     "hisq_field_export": (_I, [_P, _P, _P]),
     "hisq_field_bytes": (ctypes.c_size_t, [_P]),
     "hisq_dslash": (_I, [_P, _I, _P, _P, _I, _I, _P]),
+    "hisq_rational_apply": (_I, [_P, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _D, _P, _P,
+                                 ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
     "hisq_dslash_field": (_I, [_P, _I, _P, _P, _P]),
     "hisq_mdagm": (_I, [_P, _D, _P, _P, _I, _I, _P]),
     "hisq_mdagm_noalloc": (_I, [_P, _D, _P, _P, _I, _P]),
@@ -233,6 +235,18 @@ class Context:
         tp = (ctypes.c_double * n)(*tol) if tol is not None else None
         rc = self.check(lib().hisq_multishift_cg(self.h, float(m), n, sig, _ptr(b), xp, tp, ctypes.byref(o),
                                                  ctypes.byref(st), _ptr(residuals)))
+        return rc, st
+
+
+    def rational_apply(self, m, alpha0, alpha, sigma, b, x, opts=None, residuals=None, **kw):
+        """x = alpha0 b + sum_s alpha_s (A + sigma_s)^-1 b (hisq_rational_apply)."""
+        o = opts or self.solve_opts(**kw)
+        st = Stats()
+        n = len(sigma)
+        al = (ctypes.c_double * n)(*[float(v) for v in alpha])
+        sg = (ctypes.c_double * n)(*[float(v) for v in sigma])
+        rc = self.check(lib().hisq_rational_apply(self.h, float(m), n, al, sg, float(alpha0), _ptr(b), _ptr(x),
+                                                  ctypes.byref(o), ctypes.byref(st), _ptr(residuals)))
         return rc, st
 
 

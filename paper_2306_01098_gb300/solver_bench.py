@@ -3,6 +3,7 @@
   python -m paper_2306_01098_gb300.solver_bench --workload batched   # 64^3 x 16
   python -m paper_2306_01098_gb300.solver_bench --workload large     # 96^3 x 24, 12-real links
   python -m paper_2306_01098_gb300.solver_bench --workload uneven    # 32 uneven lattices, batched
+  python -m paper_2306_01098_gb300.solver_bench --workload rational  # r(A) b ~ A^-1/2 b, 32^3 x 8
 
 batched: multi-RHS CG for nrhs in {1, 4, 8, 16} (16-bit links, FP32 vectors, FP64 reliable
          updates), time per right-hand side against plain FP64 CG with one right-hand side, and
@@ -166,12 +167,59 @@ def uneven(reps=3):
     return rows
 
 
+def rational_workload(reps=2, nterm=24):
+    """r(A) b ~ A^-1/2 b on the 32^3 x 8 workload (eps 0.5, m 0.01): nterm sinc-quadrature
+    partial fractions applied from one multi-shift solve (every shifted system to 1e-10), FP64
+    and 16-bit sloppy, against nterm independent mixed-precision CG solves; the accuracy of the
+    approximation over the spectrum bounds is reported."""
+    import numpy as np
+    import torch
+
+    from hisq_inputs import fields, rational, workloads
+    from paper_2306_01098_gb300 import hisq
+    w = workloads.MIXED_32x8
+    fat, lng = fields.recipe_links(w.dims, w.eps, w.link_seed, device="cuda")
+    ctx = hisq.Context(w.dims, fat, lng, precs=(hisq.F64, hisq.F64X, hisq.F32, hisq.F16))
+    del fat, lng
+    lo, hi = 4 * w.mass ** 2, 4 * (w.mass ** 2 + 4 * (1 + 1 / 24) ** 2)
+    a0, al, sg = rational.inv_sqrt(nterm, lo, hi)
+    lam = np.geomspace(lo, hi, 2000)
+    approx = float(max(abs(rational.evaluate(a0, al, sg, l) * np.sqrt(l) - 1) for l in lam))
+    b = fields.gaussian_source(w.dims, w.source_seed, device="cuda")[0]
+    x = torch.empty_like(b)
+    rows = [{"workload": "rational A^-1/2, 32x32x32x8", "terms": nterm, "approx_rel_err_on_spectrum": approx}]
+    for prec, name in ((hisq.F64, "f64"), (hisq.F16, "f16")):
+        res = torch.zeros(nterm, dtype=torch.float64)
+        ms, (rc, st) = _timed(lambda: ctx.rational_apply(w.mass, a0, al, sg, b, x, tol=1e-10, prec_sloppy=prec,
+                                                         prec_precise=hisq.F64, reliable_delta=0.01, residuals=res),
+                              reps)
+        rows.append({"solve": "rational_apply", "sloppy": name, "ms": ms, "iterations": st.iterations,
+                     "max_true_residual": float(res.max()), "rc": rc})
+    # the same nterm systems as independent mixed-precision CG solves on 4 m_s^2 - D_eo D_oe
+    xs = torch.empty_like(b)
+
+    def separate():
+        worst = 0.0
+        for s in sg:
+            m_s = (w.mass ** 2 + s / 4.0) ** 0.5
+            r1 = torch.zeros(1, dtype=torch.float64)
+            ctx.cg(m_s, b, xs.zero_(), tol=1e-10, prec_sloppy=hisq.F16, prec_precise=hisq.F64, reliable_delta=0.01,
+                   residuals=r1)
+            worst = max(worst, float(r1[0]))
+        return worst
+
+    ms, worst = _timed(separate, 1)
+    rows.append({"solve": "separate_mixed_cg", "systems": nterm, "ms": ms, "max_true_residual": worst})
+    ctx.close()
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["batched", "large", "uneven"], default="batched")
+    ap.add_argument("--workload", choices=["batched", "large", "uneven", "rational"], default="batched")
     ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args()
-    rows = {"batched": batched, "large": large, "uneven": uneven}[a.workload](a.reps)
+    rows = {"batched": batched, "large": large, "uneven": uneven, "rational": rational_workload}[a.workload](a.reps)
     for r in rows:
         print(json.dumps(r), flush=True)
 

@@ -66,3 +66,45 @@ def test_multishift_bad_arguments():
     with pytest.raises(hisq.HisqError) as e:
         ctx.multishift_cg(0.1, [-1.0], b, [torch.zeros_like(b)])
     assert e.value.code == hisq.EINVAL
+
+
+@pytest.mark.parametrize("sloppy", [hisq.F64, hisq.F16])
+def test_rational_apply_matches_oracle(sloppy):
+    # r(A) b = alpha0 b + sum_s alpha_s (A + sigma_s)^-1 b (24 partial fractions of A^-1/2 by
+    # sinc quadrature, alpha0 = 0.25) through hisq_rational_apply against the oracle's
+    # multi-shift evaluation of the same rational function: every shifted system to 1e-10, so
+    # the two agree within sum_s |alpha_s| 1e-10 |b| / (lambda_min + sigma_s) (asserted as 1e-8
+    # relative), and against the exact A^-1/2 within the quadrature's error
+    from hisq_inputs import rational
+    dims, m = (8, 8, 8, 12), 0.1
+    fat, lng = fields.recipe_links(dims, 0.3, 1000)
+    ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=(hisq.F64, hisq.F64X, hisq.F32, hisq.F16))
+    b = fields.gaussian_source(dims, 2600)[0]
+    lo, hi = 4 * m * m, 4 * (m * m + 4 * (1 + 1 / 24) ** 2)
+    a0, al, sg = rational.inv_sqrt(24, lo, hi)
+    a0 = 0.25
+    x = torch.empty_like(b).cuda()
+    res = torch.zeros(len(sg), dtype=torch.float64)
+    rc, st = ctx.rational_apply(m, a0, al, sg, b.cuda(), x, tol=1e-10, prec_sloppy=sloppy, prec_precise=hisq.F64,
+                                residuals=res)
+    assert rc == hisq.OK and float(res.max()) <= 1e-10
+    want, res_o = oracle.rational_apply(dims, fat.numpy(), lng.numpy(), m, a0, al, sg, b.numpy(), tol=1e-12)
+    got = x.cpu().numpy()
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    print(f"sloppy {sloppy}: {st.iterations} iterations, rel. diff from the oracle {rel:.2e}")
+    assert rel <= 1e-8
+    ctx.close()
+
+
+def test_rational_apply_bad_arguments():
+    dims = (4, 4, 4, 6)
+    fat, lng = fields.recipe_links(dims, 0.3, 1000)
+    ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=(hisq.F64,))
+    b = fields.gaussian_source(dims, 2601)[0].cuda()
+    x = torch.empty_like(b)
+    for al, sg in (([1.0], [-1.0]), ([float("nan")], [1.0]), ([1.0] * 65, [1.0] * 65)):
+        with pytest.raises(hisq.HisqError):
+            ctx.rational_apply(0.1, 0.0, al, sg, b, x, prec_sloppy=hisq.F64)
+    with pytest.raises(hisq.HisqError):  # b and x overlap
+        ctx.rational_apply(0.1, 0.0, [1.0], [1.0], b, b, prec_sloppy=hisq.F64)
+    ctx.close()
