@@ -22,6 +22,7 @@ _lib = None
 
 __all__ = [
     "build", "lib", "dslash", "dslash_site", "mdagm", "cg", "cg_fixed", "multishift_cg", "rational_apply",
+    "condensate_samples", "dense_M",
     "phase_links", "eo_index", "coords", "count_site", "net_layer", "net_layer_backward",
     "net_apply", "net_loss_grad", "net_loss_grad_residual", "fcg", "fcg_dense", "dense_A", "dense_D", "NTAP",
     "set_threads",
@@ -207,6 +208,28 @@ def rational_apply(dims, fat, lng, m, alpha0, alpha, sigma, b, tol=1e-12, phased
     for a, x in zip(alpha, xs):
         out = out + a * x
     return out, res
+
+
+def condensate_samples(dims, fat, lng, m, eta, tol=1e-12, phased=False):
+    """Re <eta_k, A^-1 eta_k> for noise vectors eta_k on even sites, one CG solve each.  Their
+    mean estimates Tr_e A^-1, and (1/V) Tr M^-1 = 4 m Tr_e A^-1 / V for M = 2m + D (the diagonal
+    blocks of M^-1 = M^+ (M M^+)^-1 are 2m (4m^2 - D^2)^-1, whose even and odd blocks have the
+    same spectrum)."""
+    eta = np.asarray(eta, dtype=np.complex128)
+    out = np.empty(eta.shape[0])
+    for k in range(eta.shape[0]):
+        x, _, _, _ = cg(dims, fat, lng, m, eta[k], tol=tol, phased=phased)
+        out[k] = np.vdot(eta[k], x).real
+    return out
+
+
+def dense_M(dims, fat, lng, m, phased=False):
+    """Dense M = 2m + D on the full lattice, even sites first: [[2m, D_eo], [D_oe, 2m]]."""
+    Deo = dense_D(dims, fat, lng, 0, phased)
+    Doe = dense_D(dims, fat, lng, 1, phased)
+    n = Deo.shape[0]
+    eye = np.eye(n, dtype=np.complex128)
+    return np.block([[2 * m * eye, Deo], [Doe, 2 * m * eye]])
 
 
 def net_layer(dims, fat, lng, w, inp, cin, cout, phased=False):

@@ -291,3 +291,35 @@ def test_rational_apply_matches_dense_spectral_evaluation():
     exact = V @ ((lam ** -0.5) * (V.conj().T @ b.reshape(-1)))
     err = np.linalg.norm((x.reshape(-1) - a0 * b.reshape(-1)) - exact) / np.linalg.norm(exact)
     assert err <= 2e-3
+
+
+def test_condensate_trace_identity_4x4():
+    # Tr M^-1 over the full lattice (dense M = 2m + D) = 4 m Tr_e A^-1 (even sites)
+    dims, m = (4, 4, 4, 4), 0.1
+    fat, lng = _random_links(dims, 0.3, 49)
+    M = oracle.dense_M(dims, fat, lng, m)
+    A = oracle.dense_A(dims, fat, lng, m)
+    full = np.trace(np.linalg.inv(M))
+    want = 4 * m * np.trace(np.linalg.inv(A))
+    assert abs(full.imag) <= 1e-12 * abs(full) and abs(full - want) <= 1e-11 * abs(want)
+
+
+def test_condensate_free_field_closed_form():
+    # unit links: Tr_e A^-1 = sum over the even block's free spectrum 4 [m^2 + sum (c1 sin p + c3 sin 3p)^2]
+    dims, m, c1, c3 = (4, 4, 4, 4), 0.1, 9 / 8, -1 / 24
+    fat, lng = fields.unit_links(dims, c1, c3)
+    A = oracle.dense_A(dims, fat.numpy(), lng.numpy(), m)
+    lam = _free_spectrum(dims, m, c1, c3)[::2]
+    assert abs(np.trace(np.linalg.inv(A)).real - np.sum(1.0 / lam)) <= 1e-11 * np.sum(1.0 / lam)
+
+
+def test_condensate_basis_noise_gives_exact_trace():
+    # the estimator with every unit vector of the even sites as "noise" is the exact trace
+    dims, m = (4, 4, 4, 4), 0.1
+    fat, lng = _random_links(dims, 0.3, 50)
+    Vh = 128
+    eta = np.eye(3 * Vh, dtype=np.complex128).reshape(3 * Vh, Vh, 3)
+    s = oracle.condensate_samples(dims, fat, lng, m, eta, tol=1e-13)
+    A = oracle.dense_A(dims, fat, lng, m)
+    exact = np.trace(np.linalg.inv(A)).real
+    assert abs(s.sum() - exact) <= 1e-10 * exact
