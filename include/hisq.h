@@ -89,6 +89,20 @@ void hisq_opts_default(hisq_opts *opts);
 int hisq_create(hisq_ctx **ctx, const int dims[4], const double *fat, const double *lng,
                 const hisq_opts *opts);
 
+/* HISQ links from thin gauge links (Sec. 3.1: two levels of smearing, the first with c1 1/8,
+ * c3 1/16, c5 1/64, c7 1/384 for the link and its 3-, 5- and 7-link staples, a projection of
+ * the result to U(3), the second with c1 1, the same staples, the Lepage term -1/8, and the Naik
+ * link (-1/24 + eps_naik/8) W W W of the projected links).  thin: canonical [4][V][3][3]
+ * complex128 SU(3) links WITHOUT staggered phases (the layout hisq_create takes); fat, lng:
+ * the fat link X and the long (Naik) link in the same layout, ready for hisq_create (the fat
+ * link is not unitary: 12-real compression is valid for the long link only).  Host or device
+ * buffers (links_on_device), which must not overlap.  FP64 throughout; the U(3) projection is
+ * the unitary polar factor (Newton iteration).  Synchronises before returning.  Returns
+ * HISQ_EINVAL for bad dims, HISQ_ENOMEM, HISQ_ECUDA, or HISQ_EDEVICE if a first-level link was
+ * singular (no projection). */
+int hisq_smear_links(const int dims[4], const double *thin, double *fat, double *lng, double eps_naik,
+                     int links_on_device, void *stream);
+
 /* Release all device memory of the context.  NULL is accepted. */
 void hisq_destroy(hisq_ctx *ctx);
 
@@ -239,6 +253,18 @@ int hisq_multishift_cg(hisq_ctx *ctx, double m, int nshift, const double *sigma,
 int hisq_rational_apply(hisq_ctx *ctx, double m, int nterm, const double *alpha, const double *sigma,
                         double alpha0, const double *b, double *x, const hisq_solve_opts *opts,
                         hisq_stats *stats, double *residuals);
+
+/* Stochastic estimate of the chiral condensate (1/V) Tr M^-1, M = 2m + D (the measurement the
+ * paper runs with its CG, Sec. 3): Tr M^-1 = 4m Tr_e A^-1 (D only connects even and odd sites;
+ * the odd block of (M M^+)^-1 has the even block's spectrum), and Tr_e A^-1 is estimated by
+ * Re <eta_k, A^-1 eta_k> over the caller's noise vectors, solved by multi-RHS CG (up to 64
+ * vectors per solve) with opts (zero initial guesses).  eta: device [nnoise][Vh][3] complex128
+ * on even sites (Z2 or Gaussian components: unbiased when E[eta eta^+] = 1), nnoise in 1..4096,
+ * m > 0.
+ * samples (host, may be NULL): the nnoise values Re <eta_k, A^-1 eta_k>; pbp (host, may be
+ * NULL): 4 m mean(samples) / V.  Allocates the solutions for the call; synchronises. */
+int hisq_condensate(hisq_ctx *ctx, double m, int nnoise, const double *eta, const hisq_solve_opts *opts,
+                    double *samples, double *pbp, hisq_stats *stats);
 
 /* ------------------------------------------------------------------ batches of lattices */
 /* Several lattices of different sizes (each its own context, links and mass) in single

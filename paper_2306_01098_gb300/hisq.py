@@ -78,6 +78,9 @@ _SIGS = {
     "hisq_field_export": (_I, [_P, _P, _P]),
     "hisq_field_bytes": (ctypes.c_size_t, [_P]),
     "hisq_dslash": (_I, [_P, _I, _P, _P, _I, _I, _P]),
+    "hisq_condensate": (_I, [_P, _D, _I, _P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(_D),
+                             ctypes.POINTER(Stats)]),
+    "hisq_smear_links": (_I, [ctypes.POINTER(_I), _P, _P, _P, _D, _I, _P]),
     "hisq_rational_apply": (_I, [_P, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _D, _P, _P,
                                  ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
     "hisq_dslash_field": (_I, [_P, _I, _P, _P, _P]),
@@ -238,6 +241,19 @@ class Context:
         return rc, st
 
 
+    def condensate(self, m, eta, opts=None, **kw):
+        """(pbp, samples, rc, stats): (1/V) Tr M^-1 estimated from noise vectors (hisq_condensate)."""
+        import numpy as np
+        o = opts or self.solve_opts(**kw)
+        st = Stats()
+        n = eta.numel() // (self.Vh * 3)
+        samples = np.zeros(n)
+        pbp = ctypes.c_double()
+        rc = self.check(lib().hisq_condensate(self.h, float(m), n, _ptr(eta), ctypes.byref(o),
+                                              samples.ctypes.data_as(ctypes.c_void_p), ctypes.byref(pbp),
+                                              ctypes.byref(st)))
+        return pbp.value, samples, rc, st
+
     def rational_apply(self, m, alpha0, alpha, sigma, b, x, opts=None, residuals=None, **kw):
         """x = alpha0 b + sum_s alpha_s (A + sigma_s)^-1 b (hisq_rational_apply)."""
         o = opts or self.solve_opts(**kw)
@@ -248,6 +264,19 @@ class Context:
         rc = self.check(lib().hisq_rational_apply(self.h, float(m), n, al, sg, float(alpha0), _ptr(b), _ptr(x),
                                                   ctypes.byref(o), ctypes.byref(st), _ptr(residuals)))
         return rc, st
+
+
+def smear_links(dims, thin, eps_naik=0.0, stream=None):
+    """(fat, long) HISQ links from thin links (hisq_smear_links); tensors on thin's device."""
+    import torch
+    fat = torch.empty_like(thin)
+    lng = torch.empty_like(thin)
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    rc = lib().hisq_smear_links(d, _ptr(thin), _ptr(fat), _ptr(lng), float(eps_naik), int(thin.is_cuda),
+                                _stream(stream))
+    if rc != OK:
+        raise HisqError(rc, lib().hisq_strerror(rc).decode())
+    return fat, lng
 
 
 class Batch:

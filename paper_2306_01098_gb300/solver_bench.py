@@ -4,6 +4,7 @@
   python -m paper_2306_01098_gb300.solver_bench --workload large     # 96^3 x 24, 12-real links
   python -m paper_2306_01098_gb300.solver_bench --workload uneven    # 32 uneven lattices, batched
   python -m paper_2306_01098_gb300.solver_bench --workload rational  # r(A) b ~ A^-1/2 b, 32^3 x 8
+  python -m paper_2306_01098_gb300.solver_bench --workload smear     # HISQ link smearing
 
 batched: multi-RHS CG for nrhs in {1, 4, 8, 16} (16-bit links, FP32 vectors, FP64 reliable
          updates), time per right-hand side against plain FP64 CG with one right-hand side, and
@@ -214,12 +215,43 @@ def rational_workload(reps=2, nterm=24):
     return rows
 
 
+def smear_workload(reps=2):
+    """HISQ link smearing (hisq_smear_links, FP64) on the 32^3 x 8 and 96^3 x 24 thin links, and
+    the 32^3 x 8 solve (m 0.01) with the smeared operator: mixed precision vs plain FP64 CG."""
+    import torch
+
+    from hisq_inputs import fields, workloads
+    from paper_2306_01098_gb300 import hisq
+    rows = []
+    for w in (workloads.MIXED_32x8, workloads.LARGE_96x24):
+        thin, _ = fields.recipe_links(w.dims, w.eps, w.link_seed, device="cuda")
+        ms, (fat, lng) = _timed(lambda: hisq.smear_links(w.dims, thin), reps)
+        links = 4 * thin.shape[1]
+        rows.append({"op": "smear_links", "lattice": "x".join(map(str, w.dims)), "ms": ms,
+                     "links_per_s": links / (ms * 1e-3)})
+        if w is workloads.MIXED_32x8:
+            del thin
+            ctx = hisq.Context(w.dims, fat, lng, precs=(hisq.F64, hisq.F16))
+            b = fields.gaussian_source(w.dims, w.source_seed, device="cuda")[0]
+            x = torch.zeros_like(b)
+            for prec, name in ((hisq.F64, "f64"), (hisq.F16, "f16")):
+                ms, (rc, st) = _timed(lambda: ctx.cg(w.mass, b, x.zero_(), tol=w.tol, prec_sloppy=prec,
+                                                     prec_precise=hisq.F64, reliable_delta=0.01), reps)
+                rows.append({"solve": "cg_smeared_links", "sloppy": name, "ms": ms, "iterations": st.iterations,
+                             "true_residual": st.true_residual, "rc": rc})
+            ctx.close()
+        del fat, lng
+        torch.cuda.empty_cache()
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["batched", "large", "uneven", "rational"], default="batched")
+    ap.add_argument("--workload", choices=["batched", "large", "uneven", "rational", "smear"], default="batched")
     ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args()
-    rows = {"batched": batched, "large": large, "uneven": uneven, "rational": rational_workload}[a.workload](a.reps)
+    rows = {"batched": batched, "large": large, "uneven": uneven, "rational": rational_workload,
+            "smear": smear_workload}[a.workload](a.reps)
     for r in rows:
         print(json.dumps(r), flush=True)
 
