@@ -279,7 +279,7 @@ def run_ours(args, world, rank, local):
     st = stats[-1]
     Vh = ctx.Vh
     lb = {hisq.F32: 72, hisq.F16: 36, hisq.BF16: 36, hisq.F64X: 144}[sloppy]
-    sb = {hisq.F32: 24, hisq.F16: 16, hisq.BF16: 16, hisq.F64X: 48}[sloppy]
+    sb = {hisq.F32: 24, hisq.F16: 24, hisq.BF16: 24, hisq.F64X: 48}[sloppy]  # 16-bit links iterate FP32 vectors
     # mean over the iteration's Dslash pair: every link once, input and output spinor once,
     # plus the epilogue's reads in D_eo (p, and r in the single-reduction form)
     epi_reads = 2 if args.single_reduction else 1
