@@ -22,7 +22,7 @@ _lib = None
 
 __all__ = [
     "build", "lib", "dslash", "dslash_site", "mdagm", "cg", "cg_fixed", "multishift_cg", "rational_apply",
-    "condensate_samples", "dense_M",
+    "condensate_samples", "dense_M", "site_coords_all", "point_propagator", "meson_correlators",
     "phase_links", "eo_index", "coords", "count_site", "net_layer", "net_layer_backward",
     "net_apply", "net_loss_grad", "net_loss_grad_residual", "fcg", "fcg_dense", "dense_A", "dense_D", "NTAP",
     "set_threads",
@@ -220,6 +220,74 @@ def condensate_samples(dims, fat, lng, m, eta, tol=1e-12, phased=False):
     for k in range(eta.shape[0]):
         x, _, _, _ = cg(dims, fat, lng, m, eta[k], tol=tol, phased=phased)
         out[k] = np.vdot(eta[k], x).real
+    return out
+
+
+def site_coords_all(dims):
+    """[V][4] integer (x, y, z, t) of every canonical full-lattice index (Sec. 4.3: the
+    lexicographic index, x fastest, halved, with the odd sites after the Vh even ones)."""
+    nx, ny, nz, nt = dims
+    V = nx * ny * nz * nt
+    lex = np.arange(V)
+    x = lex % nx
+    y = (lex // nx) % ny
+    z = (lex // (nx * ny)) % nz
+    t = lex // (nx * ny * nz)
+    canon = lex // 2 + (V // 2) * ((x + y + z + t) % 2)
+    out = np.empty((V, 4), dtype=np.int64)
+    out[canon] = np.stack([x, y, z, t], axis=1)
+    return out
+
+
+def point_propagator(dims, fat, lng, m, src, tol=1e-12, phased=False):
+    """G = M^-1 on the three colour point sources at site `src` = (x, y, z, t), M = 2m + D on
+    the full lattice: [3][V][3] complex (source colour, canonical site, sink colour).
+
+    Solves through the even-odd reduction that the paper's solvers use (Sec. 3.2): for
+    M (x_e, x_o) = (b_e, b_o), the even part obeys A x_e = 2m b_e - D_eo b_o with
+    A = 4m^2 - D_eo D_oe, and the odd part follows as x_o = (b_o - D_oe x_e) / (2m).
+    The even system is solved by the oracle's CG to `tol`."""
+    Vh = _vol(dims) // 2
+    ci = eo_index(dims, src)
+    p, s = divmod(ci, Vh)
+    b = np.zeros((2, 3, Vh, 3), dtype=np.complex128)  # [parity][source colour][site][colour]
+    for c in range(3):
+        b[p, c, s, c] = 1.0
+    rhs = 2 * m * b[0] - dslash(dims, fat, lng, b[1], 0, phased)
+    G = np.empty((3, 2 * Vh, 3), dtype=np.complex128)
+    for c in range(3):
+        xe, _, _, _ = cg(dims, fat, lng, m, rhs[c], tol=tol, phased=phased)
+        G[c, :Vh] = xe
+        G[c, Vh:] = (b[1, c] - dslash(dims, fat, lng, xe, 1, phased)) / (2 * m)
+    return G
+
+
+def meson_correlators(dims, G, src, direction):
+    """Point-source staggered meson correlators along `direction` (0..3 = x, y, z, t) from a
+    propagator G [3][V][3] of point_propagator (the hadronic correlators of Sec. 3.3, "along
+    any direction", with point sources):
+
+      C[S][tau] = sum over sites x with (x_d - src_d) mod N_d = tau of
+                  (-1)^(sum over i in S of (x_{e_i} - src_{e_i})) * sum_{a,b} |G_ab(x, src)|^2,
+
+    where e_0 < e_1 < e_2 are the three directions other than d and bit i of S = 0..7
+    selects e_i.  These are the eight local staggered meson channels (sign factors from the
+    spin-taste phases of the transverse directions); S = 0 is the Goldstone pion.
+    Returns [8][N_d] float64."""
+    coords = site_coords_all(dims)
+    w = np.sum(np.abs(np.asarray(G)) ** 2, axis=(0, 2))  # per canonical site
+    d = int(direction)
+    trans = [mu for mu in range(4) if mu != d]
+    nd = dims[d]
+    tau = (coords[:, d] - src[d]) % nd
+    out = np.zeros((8, nd))
+    for S in range(8):
+        parity = np.zeros(len(w), dtype=np.int64)
+        for i, mu in enumerate(trans):
+            if S >> i & 1:
+                parity += coords[:, mu] - src[mu]
+        sign = np.where(parity % 2 == 0, 1.0, -1.0)
+        out[S] = np.bincount(tau, weights=sign * w, minlength=nd)
     return out
 
 
