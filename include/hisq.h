@@ -266,6 +266,25 @@ int hisq_rational_apply(hisq_ctx *ctx, double m, int nterm, const double *alpha,
 int hisq_condensate(hisq_ctx *ctx, double m, int nnoise, const double *eta, const hisq_solve_opts *opts,
                     double *samples, double *pbp, hisq_stats *stats);
 
+/* Point-source staggered meson correlators along one direction (the hadronic correlation
+ * functions with point sources of Sec. 3.3, "along any direction").  G = M^-1 on the three
+ * colour point sources at site src = {x, y, z, t}, M = 2m + D on the full lattice, from one
+ * three-RHS CG solve of the even-odd system (Sec. 3.2): A x_e = 2m b_e - D_eo b_o,
+ * x_o = (b_o - D_oe x_e) / (2m), with opts' precisions and tolerance (zero initial guesses;
+ * the FP64 operator must be built: HISQ_ENOTBUILT otherwise).
+ * corr (host, required): [8][N_d] doubles, d = direction (0..3 = x, y, z, t),
+ *   corr[S][tau] = sum over sites x with (x_d - src_d) mod N_d = tau of
+ *                  (-1)^(sum over i in S of (x_{e_i} - src_{e_i})) sum_{a,b} |G_ab(x, src)|^2,
+ *   e_0 < e_1 < e_2 the three other directions, bit i of S selecting e_i: the eight local
+ *   staggered channels, S = 0 the Goldstone pion.  Slice sums are reduced in a fixed order
+ *   (the same inputs give the same bits).
+ * prop (device, may be NULL): receives G as complex128 [3][V][3] (source colour, canonical
+ *   full-lattice site with the Vh even sites first, sink colour), 16-byte aligned, 144 V bytes.
+ * m > 0, src inside the lattice.  Allocates its workspace for the call; synchronises.
+ * Returns HISQ_ENOTCONVERGED (corr still formed) if the solve missed the tolerance. */
+int hisq_meson_correlators(hisq_ctx *ctx, double m, const int src[4], int direction,
+                           const hisq_solve_opts *opts, double *corr, double *prop, hisq_stats *stats);
+
 /* ------------------------------------------------------------------ batches of lattices */
 /* Several lattices of different sizes (each its own context, links and mass) in single
  * launches.  The paper runs one lattice at a time and has no counterpart; the Dslash of a

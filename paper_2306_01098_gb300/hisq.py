@@ -80,6 +80,8 @@ _SIGS = {
     "hisq_dslash": (_I, [_P, _I, _P, _P, _I, _I, _P]),
     "hisq_condensate": (_I, [_P, _D, _I, _P, ctypes.POINTER(SolveOpts), _P, ctypes.POINTER(_D),
                              ctypes.POINTER(Stats)]),
+    "hisq_meson_correlators": (_I, [_P, _D, ctypes.POINTER(_I), _I, ctypes.POINTER(SolveOpts), _P, _P,
+                                    ctypes.POINTER(Stats)]),
     "hisq_smear_links": (_I, [ctypes.POINTER(_I), _P, _P, _P, _D, _I, _P]),
     "hisq_rational_apply": (_I, [_P, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _D, _P, _P,
                                  ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
@@ -253,6 +255,19 @@ class Context:
                                               samples.ctypes.data_as(ctypes.c_void_p), ctypes.byref(pbp),
                                               ctypes.byref(st)))
         return pbp.value, samples, rc, st
+
+    def meson_correlators(self, m, src, direction, prop=None, opts=None, **kw):
+        """(corr [8][N_d], rc, stats): point-source staggered meson correlators along
+        `direction` (hisq_meson_correlators); `prop` (device [3][V][3] complex128) receives G."""
+        import numpy as np
+        o = opts or self.solve_opts(**kw)
+        st = Stats()
+        corr = np.zeros((8, self.dims[direction]))
+        s = (ctypes.c_int * 4)(*[int(v) for v in src])
+        rc = self.check(lib().hisq_meson_correlators(self.h, float(m), s, int(direction), ctypes.byref(o),
+                                                     corr.ctypes.data_as(ctypes.c_void_p), _ptr(prop),
+                                                     ctypes.byref(st)))
+        return corr, rc, st
 
     def rational_apply(self, m, alpha0, alpha, sigma, b, x, opts=None, residuals=None, **kw):
         """x = alpha0 b + sum_s alpha_s (A + sigma_s)^-1 b (hisq_rational_apply)."""

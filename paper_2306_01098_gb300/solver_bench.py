@@ -5,6 +5,7 @@
   python -m paper_2306_01098_gb300.solver_bench --workload uneven    # 32 uneven lattices, batched
   python -m paper_2306_01098_gb300.solver_bench --workload rational  # r(A) b ~ A^-1/2 b, 32^3 x 8
   python -m paper_2306_01098_gb300.solver_bench --workload smear     # HISQ link smearing
+  python -m paper_2306_01098_gb300.solver_bench --workload meson     # point-source correlators
 
 batched: multi-RHS CG for nrhs in {1, 4, 8, 16} (16-bit links, FP32 vectors, FP64 reliable
          updates), time per right-hand side against plain FP64 CG with one right-hand side, and
@@ -245,13 +246,35 @@ def smear_workload(reps=2):
     return rows
 
 
+def meson_workload(reps=3):
+    """Point-source meson correlators (hisq_meson_correlators) on the 32^3 x 8 workload (eps 0.5,
+    m 0.01) along t: the three-colour multi-RHS solve to 1e-10 with 16-bit and FP64 sloppy
+    operators, the call's total time against the time of its solve."""
+    from hisq_inputs import fields, workloads
+    from paper_2306_01098_gb300 import hisq
+    w = workloads.MIXED_32x8
+    fat, lng = fields.recipe_links(w.dims, w.eps, w.link_seed, device="cuda")
+    ctx = hisq.Context(w.dims, fat, lng, precs=(hisq.F64, hisq.F32, hisq.F16))
+    del fat, lng
+    src = (5, 17, 30, 3)
+    rows = []
+    for prec, name in ((hisq.F16, "f16"), (hisq.F64, "f64")):
+        ms, (corr, rc, st) = _timed(lambda: ctx.meson_correlators(w.mass, src, 3, tol=w.tol, prec_sloppy=prec,
+                                                                  prec_precise=hisq.F64, reliable_delta=0.01), reps)
+        rows.append({"op": "meson_correlators", "lattice": "x".join(map(str, w.dims)), "sloppy": name, "ms": ms,
+                     "solve_ms": 1e3 * st.seconds, "iterations": st.iterations, "true_residual": st.true_residual,
+                     "pion": [float(v) for v in corr[0]], "rc": rc})
+    ctx.close()
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["batched", "large", "uneven", "rational", "smear"], default="batched")
+    ap.add_argument("--workload", choices=["batched", "large", "uneven", "rational", "smear", "meson"], default="batched")
     ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args()
     rows = {"batched": batched, "large": large, "uneven": uneven, "rational": rational_workload,
-            "smear": smear_workload}[a.workload](a.reps)
+            "smear": smear_workload, "meson": meson_workload}[a.workload](a.reps)
     for r in rows:
         print(json.dumps(r), flush=True)
 
