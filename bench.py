@@ -135,6 +135,50 @@ def oracle_sample(seconds_budget: float, fp64_iters: int):
             "per_iteration_ms": per_iter_ms}
 
 
+def oracle_table():
+    """--oracle-table: the FP64 oracle (OpenMP C) on the host cores with one thread and with all
+    cores, one JSON line per row: full CG solves on 8^4 (eps 0.3, m 0.1) and on the 32^3 x 8
+    solver workload (all cores; one thread: a 10-iteration sample scaled to the solve's
+    iteration count), and the time per CG iteration on 64^3 x 16 (eps 0.3, m 0.01).  The thread
+    count is set with omp_set_num_threads between the oracle's parallel regions."""
+    import oracle
+    from hisq_inputs import fields
+    cores = os.cpu_count() or 1
+
+    def emit(row):
+        row.update({"kind": "oracle", "host_cores": cores})
+        print(json.dumps(row), flush=True)
+
+    for name, dims, eps, lseed, sseed, m, full in (
+            ("8^4", (8, 8, 8, 8), 0.3, 1000, 2000, 0.1, "both"),
+            ("32^3x8", DIMS, EPS, LINK_SEED, SRC_SEED, MASS, "all"),
+            ("64^3x16", (64, 64, 64, 16), 0.3, 1002, 2200, 0.01, "none")):
+        fat, lng = fields.recipe_links(dims, eps, lseed)
+        fat, lng = fat.numpy(), lng.numpy()
+        b = fields.gaussian_source(dims, sseed)[0].numpy()
+        iters = None
+        for threads in (cores, 1):
+            oracle.set_threads(threads)
+            if full == "both" or (full == "all" and threads == cores):
+                t0 = time.perf_counter()
+                _, iters, _, res = oracle.cg(dims, fat, lng, m, b, tol=TOL)
+                el = time.perf_counter() - t0
+                emit({"lattice": name, "threads": threads, "cg_ms": 1e3 * el, "iterations": iters,
+                      "true_residual": res, "per_iteration_ms": 1e3 * el / iters})
+            else:
+                n = 10 if full == "all" else (3 if threads > 1 else 1)
+                oracle.cg_fixed(dims, fat, lng, m, b, 1)  # warm
+                t0 = time.perf_counter()
+                oracle.cg_fixed(dims, fat, lng, m, b, n)
+                per = 1e3 * (time.perf_counter() - t0) / n
+                row = {"lattice": name, "threads": threads, "per_iteration_ms": per, "sample_iterations": n}
+                if iters:
+                    row.update({"cg_ms_extrapolated": per * iters, "iterations": iters})
+                emit(row)
+        del fat, lng, b
+    oracle.set_threads(cores)
+
+
 def run_reference(args, world, rank):
     """--impl reference: the FP64 oracle as it stands, on the host cores (rank 0 only)."""
     if rank != 0:
@@ -341,7 +385,12 @@ def main():
     ap.add_argument("--no-dslash-table", action="store_true")
     ap.add_argument("--fp64-reps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="time the FP64 oracle on the host cores (1 thread and all cores) and exit")
     args = ap.parse_args()
+    if args.oracle_table:
+        oracle_table()
+        return
     world, rank, local = dist_env()
     if world > 1:
         import torch.distributed as dist
