@@ -54,8 +54,8 @@ def test_correlators_match_oracle(dims, src):
     ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=(hisq.F64, hisq.F32))
     V = int(np.prod(dims))
     Gw = oracle.point_propagator(dims, fat.numpy(), lng.numpy(), m, src, tol=1e-13)
-    prop = torch.empty(3, V, 3, dtype=torch.complex128, device="cuda")
     for d in range(4):
+        prop = torch.full((3, V, 3), float("nan"), dtype=torch.complex128, device="cuda")  # unwritten sites show
         corr, rc, st = ctx.meson_correlators(m, src, d, prop=prop, tol=1e-10, prec_sloppy=hisq.F32,
                                              prec_precise=hisq.F64)
         assert rc == hisq.OK and st.true_residual <= 1e-10
@@ -91,7 +91,7 @@ def test_full_size_properties():
     dims, m, src = (32, 32, 32, 8), 0.01, (5, 17, 30, 3)
     fat, lng = fields.recipe_links(dims, 0.5, 1001)
     ctx = hisq.Context(dims, fat.cuda(), lng.cuda(), precs=(hisq.F64, hisq.F32, hisq.F16))
-    prop = torch.empty(3, 2 * ctx.Vh, 3, dtype=torch.complex128, device="cuda")
+    prop = torch.full((3, 2 * ctx.Vh, 3), float("nan"), dtype=torch.complex128, device="cuda")
     corr, rc, st = ctx.meson_correlators(m, src, 3, prop=prop, tol=1e-10, prec_sloppy=hisq.F16,
                                          prec_precise=hisq.F64)
     assert rc == hisq.OK and st.true_residual <= 1e-10
