@@ -369,14 +369,19 @@ int hisq_net_loss_grad(hisq_net *net, const double *b, const double *x, double *
  * starts at <b,x>/<b,b> of the first pairs.  losses (may be NULL) receives the mean loss of
  * every epoch. */
 int hisq_net_train(hisq_net *net, int npairs, const double *B, const double *X, double *losses);
+/* hisq_net_create(ctx, opts) then hisq_net_train on the npairs (b, x = A^-1 b) pairs, in one
+ * call: *net receives the trained network (owned by the caller, hisq_net_destroy), or NULL
+ * when either step fails, whose status is returned. */
+int hisq_precond_train(hisq_ctx *ctx, const hisq_net_opts *opts, int npairs, const double *B, const double *X,
+                       hisq_net **net);
 /* binary weights with a small header; load creates a network on ctx */
 int hisq_net_save(const hisq_net *net, const char *path);
 int hisq_net_load(hisq_ctx *ctx, const char *path, hisq_net **net);
 
 /* Flexible CG (inexact-preconditioner CG, Polak-Ribiere beta) on A x = b with z = K(r)
  * (net != NULL) or z = r (net == NULL: reduces to CG):
- *   alpha = <r,z>/<p,Ap>, x += alpha p, r' = r - alpha Ap, z' = K(r'),
- *   beta = <r' - r, z'>/<r,z>, p = z' + beta p.
+ *   alpha = conj(<r,z>)/<p,Ap> (<a,b> = sum conj(a) b), x += alpha p, r' = r - alpha Ap,
+ *   z' = K(r'), beta = <r' - r, z'>/<r,z>, p = z' + beta p.
  * FP64 vectors; A applied with opts->prec_precise (HISQ_F64 or HISQ_F64X); the final
  * residual is recomputed with the FP64 operator.  b, x: canonical [Vh][3] device buffers.
  * If the network output is not finite or the residual stops decreasing for 50 iterations,

@@ -363,3 +363,23 @@ int hisq_net_load(hisq_ctx *ctx, const char *path, hisq_net **out)
 }
 
 }  // extern "C"
+
+// hisq_net_create followed by hisq_net_train, the network returned only when both succeed
+extern "C" int hisq_precond_train(hisq_ctx *ctx, const hisq_net_opts *opts, int npairs, const double *B,
+                                  const double *X, hisq_net **net)
+{
+    if (!ctx) return HISQ_EINVAL;
+    if (!net) return set_error(ctx, HISQ_EINVAL, "hisq_precond_train: bad argument");
+    *net = nullptr;
+    if (npairs < 1 || !B || !X) return set_error(ctx, HISQ_EINVAL, "hisq_precond_train: bad argument");
+    hisq_net *n = nullptr;
+    int rc = hisq_net_create(ctx, opts, &n);
+    if (rc) return rc;
+    rc = hisq_net_train(n, npairs, B, X, nullptr);
+    if (rc) {
+        hisq_net_destroy(n);
+        return rc;
+    }
+    *net = n;
+    return HISQ_OK;
+}

@@ -107,6 +107,7 @@ _SIGS = {
     "hisq_net_apply": (_I, [_P, _P, _P, _P]),
     "hisq_net_loss_grad": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
     "hisq_net_train": (_I, [_P, _I, _P, _P, _P]),
+    "hisq_precond_train": (_I, [_P, ctypes.POINTER(NetOpts), _I, _P, _P, ctypes.POINTER(_P)]),
     "hisq_net_save": (_I, [_P, ctypes.c_char_p]),
     "hisq_net_load": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_P)]),
     "hisq_fcg": (_I, [_P, _D, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats)]),
@@ -357,6 +358,17 @@ class Net:
             ctx.check(lib().hisq_net_create(ctx.h, ctypes.byref(o), ctypes.byref(h)))
             self.h = h
         self.nw = lib().hisq_net_num_weights(self.h)
+
+    @classmethod
+    def trained(cls, ctx: Context, B, X, **opts):
+        """A network created and trained on the (b, x) pairs in one call (hisq_precond_train)."""
+        o = NetOpts()
+        lib().hisq_net_opts_default(ctypes.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        h = ctypes.c_void_p()
+        ctx.check(lib().hisq_precond_train(ctx.h, ctypes.byref(o), B.shape[0], _ptr(B), _ptr(X), ctypes.byref(h)))
+        return cls(ctx, handle=h)
 
     @classmethod
     def load(cls, ctx: Context, path: str):
