@@ -144,12 +144,14 @@ int hisq_dslash_field(hisq_ctx *ctx, int out_parity, const hisq_field *in, hisq_
                       void *stream);
 
 /* out = (4 m^2 - D_eo D_oe) in on even sites (A = M^+ M, Sec. 3.2 applyMdaggM);
- * canonical complex128 [nrhs][Vh][3] device buffers, no overlap. */
+ * canonical complex128 [nrhs][Vh][3] device buffers on the context's device, no overlap.
+ * Like every entry point that launches work, the call makes the context's device current. */
 int hisq_mdagm(hisq_ctx *ctx, double m, const double *in, double *out, int nrhs, int prec,
                void *stream);
 
-/* out = (4 m^2 - D_eo D_oe) in in FP64, exactly as hisq_mdagm(..., HISQ_F64, ...), but the
- * call allocates no device memory.  The paper has no counterpart: this entry point exists
+/* out = (4 m^2 - D_eo D_oe) in in FP64: equal to hisq_mdagm(..., HISQ_F64, ...)'s result up
+ * to rounding (the Dslash launch shape may differ, and with it the summation order), but
+ * the call allocates no device memory.  The paper has no counterpart: this entry point exists
  * for callers that cannot let a library allocate, such as applications whose device memory
  * belongs to another allocator or a fixed budget, and loops that must not call cudaMalloc
  * or cudaFree because those calls synchronise the whole device.
@@ -159,7 +161,8 @@ int hisq_mdagm(hisq_ctx *ctx, double m, const double *in, double *out, int nrhs,
  * device address (cudaGetSymbolAddress), so make it before any stream capture.  All calls
  * share the array: calls that can overlap on the GPU (different streams, or other threads)
  * race on it and must be serialised by the caller.  in/out: canonical complex128
- * [nrhs][Vh][3] device buffers, no overlap; stream-ordered on `stream`. */
+ * [nrhs][Vh][3] device buffers on the context's device, no overlap; the call makes the
+ * context's device current and is stream-ordered on `stream`. */
 int hisq_mdagm_noalloc(hisq_ctx *ctx, double m, const double *in, double *out, int nrhs, void *stream);
 
 /* Fix the Dslash launch shape for (link precision, vector precision, nrhs) instead of the

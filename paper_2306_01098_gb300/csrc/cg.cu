@@ -258,8 +258,34 @@ void release_work(hisq_ctx *ctx)
 // ---------------------------------------------------------------- L2 residency of the links
 // A persisting access-policy window over the sloppy link store keeps it in L2 across the
 // iterations when it fits (16-bit links of a 32^3 x 8 lattice: 75 MB of the 129 MB L2).
+// Everything the window changes is undone when the solve returns, on every return path:
+// the stream's window is cleared, the persisting lines are released and the device's
+// persisting-L2 limit is put back to the caller's value.
+static void set_stream_window(cudaStream_t st, const cudaAccessPolicyWindow &w)
+{
+    cudaStreamAttrValue v{};
+    v.accessPolicyWindow = w;
+    cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v);
+}
+
+struct L2Residency {
+    cudaStream_t st = nullptr;
+    bool window = false;  // the stream carries the window
+    bool raised = false;  // the persisting limit was raised from old_limit
+    size_t old_limit = 0;
+    ~L2Residency()
+    {
+        if (window) {
+            set_stream_window(st, cudaAccessPolicyWindow{});
+            cudaCtxResetPersistingL2Cache();
+        }
+        if (raised) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+        cudaGetLastError();
+    }
+};
+
 // mode: 0 off, 1 on, -1 automatic (on when the whole store fits in the persisting L2 limit)
-static cudaAccessPolicyWindow link_window(hisq_ctx *ctx, int ps, int mode)
+static cudaAccessPolicyWindow link_window(hisq_ctx *ctx, int ps, int mode, L2Residency &res)
 {
     cudaAccessPolicyWindow w{};
     if (mode == 0) return w;
@@ -273,7 +299,12 @@ static cudaAccessPolicyWindow link_window(hisq_ctx *ctx, int ps, int mode)
     if (mode < 0 && (store > (size_t)maxp || store > (size_t)maxw)) return w;
     size_t lim = 0;
     cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize);
-    if (lim < std::min(bytes, (size_t)maxp)) cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, std::min(bytes, (size_t)maxp));
+    const size_t want = std::min(bytes, (size_t)maxp);
+    if (lim < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess) {
+        res.raised = true;
+        res.old_limit = lim;
+    }
+    cudaGetLastError();
     cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize);
     w.base_ptr = L.base;
     w.num_bytes = bytes;
@@ -281,13 +312,6 @@ static cudaAccessPolicyWindow link_window(hisq_ctx *ctx, int ps, int mode)
     w.hitProp = cudaAccessPropertyPersisting;
     w.missProp = cudaAccessPropertyStreaming;
     return w;
-}
-
-static void set_stream_window(cudaStream_t st, const cudaAccessPolicyWindow &w)
-{
-    cudaStreamAttrValue v{};
-    v.accessPolicyWindow = w;
-    cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v);
 }
 
 // give every kernel node of a captured graph the window (explicitly, not relying on capture)
@@ -500,8 +524,11 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
     w.shape = dslash_shape(ctx, ps, w.pv, nrhs, w.p, w.t, w.rbS, st);
     w.fused = o.single_reduction != 0;
     const long per_it = w.fused ? 3 : 4; // launches per iteration
-    const cudaAccessPolicyWindow win = link_window(ctx, ps, o.l2_persist);
+    L2Residency l2res;
+    const cudaAccessPolicyWindow win = link_window(ctx, ps, o.l2_persist, l2res);
     set_stream_window(st, win);
+    l2res.st = st;
+    l2res.window = win.num_bytes > 0;
     const int ci = std::max(1, o.check_interval);
     const int interval = ps == HISQ_F64 ? (1 << 30) : std::max(1, o.reliable_interval);
     const bool prof = o.profile != 0;
@@ -623,10 +650,6 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
     const cudaMemcpyKind k_out = o.host_buffers ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     HISQ_CUDA(ctx, cudaMemcpyAsync(x, w.x64, vb, k_out, st));
     if ((rc = read_scalars(ctx, w, st))) return rc;
-    if (win.num_bytes) { // release the persisting lines and the stream's window
-        set_stream_window(st, cudaAccessPolicyWindow{});
-        cudaCtxResetPersistingL2Cache();
-    }
     // later work on the caller's stream is ordered after the solve
     HISQ_CUDA(ctx, cudaEventRecord(w.ev, st));
     HISQ_CUDA(ctx, cudaStreamWaitEvent(ust, w.ev, 0));

@@ -91,7 +91,7 @@ static DslashShape default_shape(hisq_ctx *ctx, int pv, int nrhs)
 DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in, void *out, size_t rhs_bytes,
                          cudaStream_t st)
 {
-    const int key = (pl * 8 + pv) * 256 + nrhs;
+    const long long key = tune_key(pl, pv, nrhs);
     auto it = ctx->tune.find(key);
     if (it != ctx->tune.end()) return it->second;
     DslashShape best = default_shape(ctx, pv, nrhs);
@@ -184,7 +184,7 @@ extern "C" int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, in
         site_order < -1 || site_order > 1 || (site_order == 1 && !ctx->g.zt_ok))
         return set_error(ctx, HISQ_EINVAL, "hisq_tune_set: bad shape");
     const int order = site_order >= 0 ? site_order : default_order(ctx, prec_vectors, nrhs);
-    ctx->tune[(prec_links * 8 + prec_vectors) * 256 + nrhs] = DslashShape{n_inner, threads_per_site, order};
+    ctx->tune[tune_key(prec_links, prec_vectors, nrhs)] = DslashShape{n_inner, threads_per_site, order};
     return HISQ_OK;
 }
 

@@ -196,6 +196,10 @@ struct DslashShape {
     int order = 0; // 0: sites in storage order (t slowest); 1: z and t interchanged in launch order
 };
 
+// key of a Dslash shape in the context's tuning table: link precision, vector precision and
+// the right-hand side count each in a field of its own, so no two keys collide
+inline long long tune_key(int pl, int pv, int nrhs) { return ((long long)(pl * 8 + pv) << 32) | (unsigned)nrhs; }
+
 // ---------------------------------------------------------------- batches of lattices
 constexpr int kMaxBatch = 32;
 
@@ -228,7 +232,7 @@ struct hisq_ctx {
     hisq::Geom g{};
     int links_phased = 0;
     int autotune = 1;
-    std::map<int, hisq::DslashShape> tune; // autotuned Dslash shapes
+    std::map<long long, hisq::DslashShape> tune; // autotuned Dslash shapes, keyed by hisq::tune_key
     hisq::LinkStore links[HISQ_NPREC];
     int last_error = 0;
     std::string msg;

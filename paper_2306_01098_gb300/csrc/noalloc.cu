@@ -27,18 +27,15 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchSites *
 static std::mutex g_noalloc_mu;
 static void *g_noalloc_addr[kNoAllocMaxDevices];
 
-// device address of the scratch array on `dev` (looked up with `dev` current, then cached)
+// device address of the scratch array on `dev`, which the caller has made current (looked
+// up once per device, then cached)
 static int noalloc_scratch(hisq_ctx *ctx, int dev, void **addr)
 {
     if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(ctx, HISQ_EINVAL, "hisq_mdagm_noalloc: device ordinal");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
-        int cur = -1;
-        cudaError_t e = cudaGetDevice(&cur);
-        if (e == cudaSuccess && cur != dev) e = cudaSetDevice(dev);
         void *p = nullptr;
-        if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (cur >= 0 && cur != dev) cudaSetDevice(cur);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_error(ctx, e, "hisq_mdagm_noalloc: cudaGetSymbolAddress");
         g_noalloc_addr[dev] = p;
     }
@@ -62,6 +59,8 @@ extern "C" int hisq_mdagm_noalloc(hisq_ctx *ctx, double m, const double *in, dou
     const size_t bytes = sites * 48;
     const char *a = reinterpret_cast<const char *>(in), *b = reinterpret_cast<const char *>(out);
     if (a < b + bytes && b < a + bytes) return set_error(ctx, HISQ_EINVAL, "hisq_mdagm_noalloc: in and out overlap");
+    // the kernels run on the context's device, where its links and the scratch array live
+    HISQ_CUDA(ctx, cudaSetDevice(ctx->device));
     void *scratch = nullptr;
     int rc = noalloc_scratch(ctx, ctx->device, &scratch);
     if (rc) return rc;

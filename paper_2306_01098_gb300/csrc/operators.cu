@@ -29,7 +29,7 @@ int apply_mdagm(hisq_ctx *ctx, int prec, double m, const void *in, void *tmp, vo
     if (tune) {
         sh = dslash_shape(ctx, prec, pv, nrhs, in, tmp, rhs_bytes, st);
     } else {
-        auto it = ctx->tune.find((prec * 8 + pv) * 256 + nrhs);
+        auto it = ctx->tune.find(tune_key(prec, pv, nrhs));
         sh.nr = it != ctx->tune.end() ? it->second.nr : pick_inner(pv, nrhs);
         sh.ds = it != ctx->tune.end() ? it->second.ds : (ctx->g.Vh < (1u << 20) ? 2 : 1);
         sh.order = it != ctx->tune.end() ? it->second.order : 0;
@@ -57,6 +57,7 @@ int hisq_dslash(hisq_ctx *ctx, int out_parity, const double *in, double *out, in
     if (!ctx) return HISQ_EINVAL;
     if (!in || !out || nrhs < 1 || (out_parity != 0 && out_parity != 1))
         return set_error(ctx, HISQ_EINVAL, "hisq_dslash: bad argument");
+    HISQ_CUDA(ctx, cudaSetDevice(ctx->device));
     int rc = check_prec(ctx, prec);
     if (rc) return rc;
     const size_t bytes = (size_t)nrhs * ctx->g.Vh * 48;
@@ -79,6 +80,7 @@ int hisq_dslash_field(hisq_ctx *ctx, int out_parity, const hisq_field *in, hisq_
     if (!in || !out || in->prec != out->prec || in->nrhs != out->nrhs || in == out || in->ctx != ctx ||
         out->ctx != ctx || (out_parity != 0 && out_parity != 1))
         return set_error(ctx, HISQ_EINVAL, "hisq_dslash_field: bad argument");
+    HISQ_CUDA(ctx, cudaSetDevice(ctx->device));
     int rc = check_prec(ctx, in->prec);
     if (rc) return rc;
     return launch_dslash(ctx, in->prec, out_parity, in->data, out->data, in->nrhs, in->rhs_bytes, (cudaStream_t)stream);
@@ -88,6 +90,7 @@ int hisq_mdagm(hisq_ctx *ctx, double m, const double *in, double *out, int nrhs,
 {
     if (!ctx) return HISQ_EINVAL;
     if (!in || !out || nrhs < 1) return set_error(ctx, HISQ_EINVAL, "hisq_mdagm: bad argument");
+    HISQ_CUDA(ctx, cudaSetDevice(ctx->device));
     int rc = check_prec(ctx, prec);
     if (rc) return rc;
     const size_t bytes = (size_t)nrhs * ctx->g.Vh * 48;

@@ -171,6 +171,7 @@ class Context:
             raise HisqError(rc, L.hisq_strerror(rc).decode())
         self.h = h
         self.dims = tuple(dims)
+        self.device = int(device)
         self.Vh = L.hisq_half_volume(h)
 
     def close(self):
@@ -190,17 +191,33 @@ class Context:
         return rc
 
     # ------------------------------------------------------------------ operators
+    def _nrhs(self, inp, out):
+        """Right-hand sides of an (in, out) pair of canonical [nrhs][Vh][3] complex128 vectors.
+        The C side receives only pointers, so sizes, dtypes and devices are checked here."""
+        import torch
+        for name, t in (("in", inp), ("out", out)):
+            if t.dtype != torch.complex128:
+                raise ValueError(f"{name}: complex128 expected, got {t.dtype}")
+            if not t.is_cuda or t.device.index != self.device:
+                raise ValueError(f"{name}: must live on cuda:{self.device}, the context's device")
+        n = self.Vh * 3
+        if inp.numel() == 0 or inp.numel() % n:
+            raise ValueError(f"in: {inp.numel()} elements is not a whole number of [Vh={self.Vh}][3] vectors")
+        if out.numel() != inp.numel():
+            raise ValueError(f"out has {out.numel()} elements, in has {inp.numel()}")
+        return inp.numel() // n
+
     def dslash(self, out_parity, inp, out, prec=F64, stream=None):
-        nrhs = inp.numel() // (self.Vh * 3)
+        nrhs = self._nrhs(inp, out)
         return self.check(lib().hisq_dslash(self.h, out_parity, _ptr(inp), _ptr(out), nrhs, prec, _stream(stream)))
 
     def mdagm(self, m, inp, out, prec=F64, stream=None):
-        nrhs = inp.numel() // (self.Vh * 3)
+        nrhs = self._nrhs(inp, out)
         return self.check(lib().hisq_mdagm(self.h, float(m), _ptr(inp), _ptr(out), nrhs, prec, _stream(stream)))
 
     def mdagm_noalloc(self, m, inp, out, stream=None):
         """FP64 normal operator without device allocation (fixed scratch array)."""
-        nrhs = inp.numel() // (self.Vh * 3)
+        nrhs = self._nrhs(inp, out)
         return self.check(lib().hisq_mdagm_noalloc(self.h, float(m), _ptr(inp), _ptr(out), nrhs, _stream(stream)))
 
     def tune_set(self, prec_links, prec_vectors, nrhs, n_inner, threads_per_site, site_order=-1):

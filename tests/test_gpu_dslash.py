@@ -240,6 +240,15 @@ def test_argument_errors():
     with pytest.raises(hisq.HisqError) as e:
         ctx.dslash(2, x[0].contiguous(), torch.empty_like(x[0]))
     assert e.value.code == hisq.EINVAL
+    # the binding checks what the C side cannot see behind its pointers
+    with pytest.raises(ValueError):
+        ctx.dslash(0, x, torch.empty_like(x[0]))      # out shorter than in
+    with pytest.raises(ValueError):
+        ctx.mdagm(0.1, x[:, :-1].contiguous(), torch.empty_like(x[:, :-1]))   # not whole vectors
+    with pytest.raises(ValueError):
+        ctx.mdagm(0.1, x.to(torch.complex64), torch.empty_like(x).to(torch.complex64))
+    with pytest.raises(ValueError):
+        ctx.mdagm_noalloc(0.1, x.cpu(), torch.empty_like(x).cpu())
     for bad in [(5, 4, 4, 4), (4, 4, 2, 4), (4, 4, 4, 7)]:
         with pytest.raises(hisq.HisqError):
             hisq.Context(bad, torch.zeros(4, int(np.prod(bad)), 3, 3, dtype=torch.complex128).cuda(),
@@ -283,3 +292,109 @@ def test_site_order_rejected_where_unavailable():
         ctx.tune_set(hisq.F64, hisq.F64, 1, 1, 1, 2)
     ctx.tune_set(hisq.F64, hisq.F64, 1, 1, 1, 0)
     _cache.clear()
+
+
+# ---------------------------------------------------------------- reduced precision, site by site
+# Per-site bound for 16-bit link storage with FP32 vectors.  A stored real component q of a
+# link entry carries |q - q_exact| <= u |q_exact| (u = 2^-11 for FP16, 2^-8 for BF16, round to
+# nearest), so the entry error is |dU_ij| <= u |U_ij| and, row by row (Cauchy-Schwarz),
+# |dU phi| <= u |U|_F |phi|.  For a link c V with V in SU(3), |U|_F = sqrt(3) |c|.  With 12
+# reals, rows 0 and 1 are stored that way and row 2 = conj(row0 x row1) is rebuilt from them:
+# each rebuilt entry is a difference of two products of unit-bounded entries, so its error
+# is at most 2u, and |dU|_F <= (sqrt(2) + 2 sqrt(3)) u |c|.  The FP32 arithmetic (9 complex
+# multiply-adds per hop, 16 hops, the FP64 -> FP32 input rounding) adds a few 2^-24 per hop;
+# 40 * 2^-24 covers it.  Summed over the 16 hops of the stencil:
+#     |D_gpu phi(x) - D phi(x)| <= f(u, nreal) * S(x),   S(x) = sum_hops |c_hop| |phi(x + hop)|
+# with c = 1 for the one-hop (fat = U) and 1/24 for the three-hop (long = -UUU/24) links of
+# the workloads.  This holds for every site, whatever cancellation the sum has.
+U_F16, U_BF16 = 2.0 ** -11, 2.0 ** -8
+
+
+def hop_factor(u, nreal):
+    return (np.sqrt(3.0) if nreal == 18 else np.sqrt(2.0) + 2.0 * np.sqrt(3.0)) * u + 40 * 2.0 ** -24
+
+
+def hop_magnitudes(dims, x, out_parity, c1=1.0, c3=1.0 / 24.0):
+    """S(x) for every output site (half index) of out_parity: sum over mu and the hops +-1, +-3
+    of |c| times the 2-norm of the input colour vector at the neighbour.  x: [Vh][3] field of
+    parity 1 - out_parity in canonical half-lattice order (half index = lexicographic // 2)."""
+    nx, ny, nz, nt = dims
+    V = nx * ny * nz * nt
+    lex = np.arange(V)
+    cx, cy, cz, ct = lex % nx, (lex // nx) % ny, (lex // (nx * ny)) % nz, lex // (nx * ny * nz)
+    par = (cx + cy + cz + ct) % 2
+    nrm = np.linalg.norm(np.asarray(x).reshape(V // 2, 3), axis=1)
+    full = np.zeros(V)
+    full[par == 1 - out_parity] = nrm[lex[par == 1 - out_parity] // 2]
+    full = full.reshape(nt, nz, ny, nx)
+    S = np.zeros_like(full)
+    for axis in (3, 2, 1, 0):          # x, y, z, t
+        for k, c in ((1, c1), (3, c3)):
+            S += c * (np.roll(full, -k, axis=axis) + np.roll(full, k, axis=axis))
+    S = S.reshape(V)
+    out = np.zeros(V // 2)
+    out[lex[par == out_parity] // 2] = S[par == out_parity]
+    return out
+
+
+def check_sites(got, want, S, factor, what):
+    err = np.linalg.norm(got - want, axis=-1)
+    ratio = float((err / (factor * S)).max())
+    assert np.isfinite(got).all(), what
+    assert ratio <= 1.0, f"{what}: worst site at {ratio:.3f} of its bound"
+    return ratio
+
+
+@pytest.mark.parametrize("prec,u", [(hisq.F16, U_F16), (hisq.BF16, U_BF16)])
+def test_16bit_links_every_site_bench_lattice(prec, u):
+    # the bench solve's sloppy operator: 16-bit links (18 reals), FP32 vectors, on the
+    # 32^3 x 8 workload (eps 0.5, seed 1001); every output site of both parities, one and four
+    # right-hand sides, each (n_inner, threads per site) shape
+    dims = (32, 32, 32, 8)
+    fat, lng = fields.recipe_links(dims, 0.5, 1001, device="cuda")
+    ctx = hisq.Context(dims, fat, lng, precs=(prec,))
+    fh, lh = fat.cpu().numpy(), lng.cpu().numpy()
+    del fat, lng
+    factor = hop_factor(u, 18)
+    worst = 0.0
+    for nrhs, shapes in ((1, [(1, 1), (1, 2), (1, 4)]), (4, [(4, 1), (2, 2), (1, 4)])):
+        x = fields.gaussian_source(dims, 2300 + nrhs, nrhs)
+        for p in (0, 1):
+            want = oracle.dslash(dims, fh, lh, x, p)
+            S = [hop_magnitudes(dims, x[r], p) for r in range(nrhs)]
+            for nr, ds in shapes:
+                ctx.tune_set(prec, hisq.F32, nrhs, nr, ds)
+                out = torch.full_like(x, float("nan")).cuda()
+                ctx.dslash(p, x.cuda(), out, prec=prec)
+                got = out.cpu().numpy()
+                for r in range(nrhs):
+                    worst = max(worst, check_sites(got[r], want[r], S[r], factor, (nrhs, p, nr, ds, r)))
+    print(f"{hisq.PREC_NAMES[prec]} 32^3x8: worst site at {worst:.3f} of the quantisation bound")
+
+
+@pytest.mark.parametrize("prec,u", [(hisq.F16, U_F16), (hisq.BF16, U_BF16)])
+def test_12_real_every_site_large_lattice(prec, u):
+    # 12-real 16-bit links on 64^3 x 16 (the link store, 805 MB, exceeds what L2 keeps, so
+    # n_inner > 1 reads links evict-first), every output site, one and four right-hand sides,
+    # both site orders (z and t interchanged is the default for several right-hand sides)
+    dims = (64, 64, 64, 16)
+    fat, lng = fields.recipe_links(dims, 0.3, 1002, device="cuda")
+    ctx = hisq.Context(dims, fat, lng, precs=(prec,), compression={prec: 12})
+    fh, lh = fat.cpu().numpy(), lng.cpu().numpy()
+    del fat, lng
+    factor = hop_factor(u, 12)
+    worst = 0.0
+    for nrhs, shapes in ((1, [(1, 1, 0), (1, 2, 0)]), (4, [(4, 1, 1), (2, 1, 0), (4, 2, 0)])):
+        x = fields.gaussian_source(dims, 2400 + nrhs, nrhs)
+        p = nrhs % 2
+        want = oracle.dslash(dims, fh, lh, x, p)
+        S = [hop_magnitudes(dims, x[r], p) for r in range(nrhs)]
+        for nr, ds, order in shapes:
+            ctx.tune_set(prec, hisq.F32, nrhs, nr, ds, order)
+            out = torch.full_like(x, float("nan")).cuda()
+            ctx.dslash(p, x.cuda(), out, prec=prec)
+            got = out.cpu().numpy()
+            for r in range(nrhs):
+                worst = max(worst, check_sites(got[r], want[r], S[r], factor, (nrhs, nr, ds, order, r)))
+        del want, S, x
+    print(f"{hisq.PREC_NAMES[prec]} 12-real 64^3x16: worst site at {worst:.3f} of the quantisation bound")
