@@ -239,7 +239,8 @@ def run_ours(args, world, rank, local):
     dev = f"cuda:{local}"
     fat, lng = fields.recipe_links(DIMS, EPS, LINK_SEED, device=dev)
     sloppy = {"f32": hisq.F32, "f16": hisq.F16, "bf16": hisq.BF16, "f64x": hisq.F64X}[args.sloppy]
-    ctx = hisq.Context(DIMS, fat, lng, precs=(hisq.F64, hisq.F64X, hisq.F32, hisq.F16, hisq.BF16), device=local)
+    ctx = hisq.Context(DIMS, fat, lng, precs=(hisq.F64, hisq.F64X, hisq.F32, hisq.F16, hisq.BF16), device=local,
+                       compression={sloppy: args.sloppy_reals})
     del fat, lng
     b = fields.gaussian_source(DIMS, SRC_SEED, device=dev)[0]
     x = torch.zeros_like(b)
@@ -253,7 +254,7 @@ def run_ours(args, world, rank, local):
         rc, st = ctx.cg(MASS, bb, xb, tol=TOL, prec_sloppy=prec, prec_precise=precise, reliable_interval=100,
                         l2_persist=int(args.l2_persist), use_graph=int(args.use_graph),
                         reliable_delta=args.delta, profile=profile, host_buffers=host, stream=stream,
-                        single_reduction=args.single_reduction)
+                        single_reduction=args.single_reduction, persistent=args.persistent if prec != hisq.F64 else 0)
         if rc != hisq.OK:
             raise RuntimeError(f"solve did not converge: {st.as_dict()}")
         return st
@@ -322,16 +323,36 @@ def run_ours(args, world, rank, local):
     err_vs_fp64 = float(((x - x64).norm() / x64.norm()).item())
     st = stats[-1]
     Vh = ctx.Vh
-    lb = {hisq.F32: 72, hisq.F16: 36, hisq.BF16: 36, hisq.F64X: 144}[sloppy]
+    reals = args.sloppy_reals
+    lb = {hisq.F32: 4, hisq.F16: 2, hisq.BF16: 2, hisq.F64X: 8}[sloppy] * reals
     sb = {hisq.F32: 24, hisq.F16: 24, hisq.BF16: 24, hisq.F64X: 48}[sloppy]  # 16-bit links iterate FP32 vectors
-    # mean over the iteration's Dslash pair: every link once, input and output spinor once,
-    # plus the epilogue's reads in D_eo (p, and r in the single-reduction form)
-    epi_reads = 2 if args.single_reduction else 1
-    bytes_per_launch = Vh * (16 * lb + 2 * sb) + Vh * sb * epi_reads // 2
-    d_ms = sum(s.dslash_ms for s in stats) / max(1, sum(s.dslash_timed for s in stats))
     hbm, src = peaks()
+    persistent = st.persistent_ds > 0
+    single = persistent or args.single_reduction
+    # algorithmic bytes of one sloppy iteration: each Dslash reads every link once and its input
+    # and output once; D_eo's epilogue reads p (and r in the single-reduction form); the
+    # updates read and write x, r, p (and read Ap): two-reduction 14, single-reduction 13 records
+    iter_bytes = Vh * (32 * lb + (13 if single else 14) * sb)
+    # one reliable update: the FP64 normal operator (two FP64 Dslash applications, p read by
+    # the epilogue) and the FP64 vector passes around it (b, Ax, r; x_hi and x_lo; r back)
+    ru_bytes = Vh * (2 * (16 * 144 + 2 * 48) + 48 + 3 * 48 + 2 * 48 + 2 * sb + 48 + sb)
+    solve_bytes = st.iterations * iter_bytes + st.reliable_updates * ru_bytes
+    if persistent:
+        # the dominant kernel is the persistent phase kernel: all sloppy iterations of a phase
+        kname = f"cg_phase_{args.sloppy}_{reals}_32x32x32x8"
+        launches = sum(s.phase_launches for s in stats)
+        iters_timed = sum(s.phase_iterations for s in stats)
+        d_ms = sum(s.phase_ms for s in stats) / max(1, launches)
+        bytes_per_launch = iter_bytes * iters_timed / max(1, launches)
+    else:
+        # mean over the iteration's Dslash pair: every link once, input and output spinor once,
+        # plus the epilogue's reads in D_eo (p, and r in the single-reduction form)
+        kname = f"dslash_{args.sloppy}_{reals}_32x32x32x8"
+        epi_reads = 2 if args.single_reduction else 1
+        bytes_per_launch = Vh * (16 * lb + 2 * sb) + Vh * sb * epi_reads // 2
+        launches = sum(s.dslash_timed for s in stats)
+        d_ms = sum(s.dslash_ms for s in stats) / max(1, launches)
     achieved = bytes_per_launch / (d_ms * 1e-3) / 1e9
-    kname = f"dslash_{args.sloppy}_18_32x32x32x8"
     clocks = clk.summary()
     if rank != 0:
         return
@@ -348,17 +369,22 @@ def run_ours(args, world, rank, local):
                    "reliable_interval": 100, "reliable_delta": args.delta,
                    "l2": "flushed between timed solves (256 MB write)",
                    "l2_persist_links": {-1: "auto", 0: "off", 1: "on"}[args.l2_persist],
-                   "iteration_loop": "CUDA graph WHILE node" if args.use_graph else "direct launches",
-                   "reductions_per_iteration": 1 if args.single_reduction else 2,
+                   "sloppy_link_reals": reals,
+                   "iteration_loop": (f"one persistent cooperative kernel per phase ({st.persistent_ds} threads/site)"
+                                      if persistent else
+                                      "CUDA graph WHILE node" if args.use_graph else "direct launches"),
+                   "reductions_per_iteration": 1 if single else 2,
                    "parallelism": f"replicas x{world}"},
         "iterations": st.iterations, "reliable_updates": st.reliable_updates, "true_residual": st.true_residual,
         "error_vs_fp64": err_vs_fp64, "fp64_cg_ms": fp64_ms, "fp64_iterations": st64.iterations,
         "speedup_vs_fp64_cg": fp64_ms / ms_per_solve if fp64_ms else None, "timed_total_ms": total_ms,
+        "solve_algorithmic_bytes": solve_bytes,
+        "time_to_solution_roof_frac": solve_bytes / (ms_per_solve * 1e-3) / 1e9 / hbm,
         "dslash_64x64x64x16": table,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic_for(kname), "kernel": kname, "peak_source": src,
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": d_ms * 1e3,
-                     "launches_timed": sum(s.dslash_timed for s in stats)},
+                     "launches_timed": launches},
         "cpu_baseline": cb,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(b.numel() * 16),
                 "d2h_bytes_per_step": int(b.numel() * 16)},
@@ -380,6 +406,9 @@ def main():
     ap.add_argument("--delta", type=float, default=0.01)
     ap.add_argument("--use-graph", type=int, default=1, help="0: direct launches (for ncu launch lists)")
     ap.add_argument("--single-reduction", type=int, default=0, help="1: one grid reduction per CG iteration")
+    ap.add_argument("--persistent", type=int, default=-1,
+                    help="-1: the library's choice; 0: multi-kernel loop; 1, 2, 4: persistent kernel, threads per site")
+    ap.add_argument("--sloppy-reals", type=int, default=18, choices=[18, 12], help="sloppy link compression")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash-table", action="store_true")

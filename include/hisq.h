@@ -210,6 +210,23 @@ typedef struct {
                               before one pass updates x, r and p (three launches per
                               iteration); 0 (default): the two-reduction form, |r'|^2
                               reduced from the updated r (four launches)                   */
+    int persistent;        /* CG with one right-hand side, no shifts and FP32 iteration
+                              vectors (sloppy F32, F16 or BF16): run all sloppy iterations
+                              between two reliable updates inside ONE cooperatively launched
+                              kernel, in the single-reduction arrangement: one block per SM,
+                              each owning a range of sites whose x, r, p and Ap stay in
+                              shared memory, bounded grid-wide barriers between the steps.
+                              Used when the range fits (Vh up to about 2100 sites per SM).
+                              -1 (default): when eligible, launch shape 2; 0: never; 1 to 4:
+                              when eligible, with that launch shape (threads per block and
+                              load scheduling: 1 = 1024, 2 = 512 with the four hops of a
+                              direction loaded before their products, 3 = 896 and 4 = 1024
+                              likewise).  A barrier wait that runs out (about 1 s) ends the
+                              launch early and the solve returns HISQ_EDEVICE               */
+    int selftest_wait;     /* 1: test of that bounded wait: in the first persistent launch one
+                              block leaves without arriving at the first barrier, whose wait
+                              (bounded to 1 ms here) runs out in every other block; the
+                              solve returns HISQ_EDEVICE and the context stays usable      */
 } hisq_solve_opts;
 
 typedef struct {
@@ -224,6 +241,12 @@ typedef struct {
                                 is the average duration of one sloppy Dslash launch          */
     double bytes_moved;      /* algorithmic bytes of the sloppy Dslash applications           */
     long kernels;            /* kernel launches issued by the call (graph nodes included)     */
+    double phase_ms;         /* persistent solves with profile = 1: summed event time of the
+                                persistent phase launches                                     */
+    long phase_iterations;   /* iterations those launches ran: phase_ms / phase_iterations is
+                                the time of one sloppy iteration inside the persistent kernel */
+    long phase_launches;     /* number of timed persistent launches                           */
+    int persistent_ds;       /* launch shape of the persistent kernel (0: not used)           */
 } hisq_stats;
 
 void hisq_solve_opts_default(hisq_solve_opts *o);

@@ -359,6 +359,18 @@ template <> struct Prec<HISQ_F32> : FloatArith {
 #pragma unroll
         for (int i = 0; i < 3; i++) p[i] = make_float2(a.v[2 * i], a.v[2 * i + 1]);
     }
+    // ordinary (coherent) loads, for vectors that other blocks of the same launch write
+    // between grid barriers: the read-only path of load() may serve such data stale
+    __device__ static void load_coh(const void *base, uint32_t s, Vec &v)
+    {
+        const float2 *p = reinterpret_cast<const float2 *>(static_cast<const char *>(base) + (size_t)s * SB);
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const float2 d = p[i];
+            v.v[2 * i] = d.x;
+            v.v[2 * i + 1] = d.y;
+        }
+    }
 };
 
 // 16-bit storage; spinor record = 3 x (2 x 16-bit) + float scale

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "blas.cuh"
+#include "cg_phase.cuh"
 #include "dslash.cuh"
 #include "solver.cuh"
 
@@ -151,6 +152,8 @@ void SolverWork::release()
     h_sc = nullptr;
     if (h_shift) cudaFreeHost(h_shift);
     h_shift = nullptr;
+    if (h_status) cudaFreeHost(h_status);
+    h_status = nullptr;
     if (st) cudaStreamDestroy(st);
     st = nullptr;
     if (ev) cudaEventDestroy(ev);
@@ -233,11 +236,14 @@ int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out)
     W.counter = reinterpret_cast<unsigned *>(tmp);
     A(&tmp, sizeof(LoopCtl));
     W.ctl = reinterpret_cast<LoopCtl *>(tmp);
+    A(&tmp, sizeof(PhaseSlot) * kPhaseMaxBlocks);
+    W.phase_slots = tmp;
     A(&tmp, sizeof(double) * (nrhs + 64));
     W.shift_buf = reinterpret_cast<double *>(tmp);
     if (rc) return rc;
     if (cudaMallocHost(&W.h_sc, sizeof(Scalars) * (nrhs + 64)) != cudaSuccess ||
-        cudaMallocHost(&W.h_shift, sizeof(double) * (nrhs + 64)) != cudaSuccess)
+        cudaMallocHost(&W.h_shift, sizeof(double) * (nrhs + 64)) != cudaSuccess ||
+        cudaMallocHost(&W.h_status, sizeof(DevStatus)) != cudaSuccess)
         return set_error(ctx, HISQ_ENOMEM, "pinned scalars");
     if (cudaStreamCreateWithFlags(&W.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&W.ev, cudaEventDisableTiming) != cudaSuccess)
@@ -438,6 +444,59 @@ static int build_loop_graph(hisq_ctx *ctx, SolverWork &w, double m, const cudaAc
     return HISQ_OK;
 }
 
+// ---------------------------------------------------------------- persistent phases
+cudaError_t phase_launch_HISQ_F32(const PhaseArgs &a, int nreal, int ds, int sms, cudaStream_t st);
+cudaError_t phase_launch_HISQ_F16(const PhaseArgs &a, int nreal, int ds, int sms, cudaStream_t st);
+cudaError_t phase_launch_HISQ_BF16(const PhaseArgs &a, int nreal, int ds, int sms, cudaStream_t st);
+
+// launch shape of the persistent kernel for o.persistent (0: the multi-kernel loop)
+static int persistent_ds(hisq_ctx *ctx, const SolverWork &w, const hisq_solve_opts &o, bool shifted)
+{
+    if (o.persistent == 0 || w.nrhs != 1 || shifted || w.pv != HISQ_F32 || ctx->batch) return 0;
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device) != cudaSuccess || !coop) {
+        cudaGetLastError();
+        return 0;
+    }
+    // the block's x, r, p and Ap must fit in shared memory
+    if (phase_chunk(w.Vh, ctx->sm_count) == 0) return 0;
+    if (o.persistent >= 1 && o.persistent <= 4) return o.persistent;
+    return 2;
+}
+
+// the sloppy iterations of one phase (at most cap) in one cooperative launch
+static int launch_persistent_phase(hisq_ctx *ctx, SolverWork &w, double m, int cap, int ds, int selftest,
+                                   cudaStream_t st)
+{
+    PhaseArgs a{};
+    a.doe = make_dslash_args(ctx, w.ps, 1, w.p, w.t, 1, w.rbS);
+    a.doe.zt = 0;
+    a.deo = make_dslash_args(ctx, w.ps, 0, w.t, w.Ap, 1, w.rbS);
+    a.deo.zt = 0;
+    a.deo.m4 = 4.0 * m * m;
+    a.x = w.xlo;
+    a.p = w.p;
+    a.r = w.r;
+    a.Vh = w.Vh;
+    a.sc = w.sc;
+    a.slots = static_cast<PhaseSlot *>(w.phase_slots);
+    a.status = ctx->status;
+    a.cap = cap;
+    a.selftest = selftest;
+    a.wait_ns = selftest ? 1000000ull : 1000000000ull;
+    HISQ_CUDA(ctx, cudaMemsetAsync(w.phase_slots, 0, sizeof(PhaseSlot) * kPhaseMaxBlocks, st));
+    const int nreal = ctx->links[w.ps].nreal;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (w.ps) {
+    case HISQ_F32: e = phase_launch_HISQ_F32(a, nreal, ds, ctx->sm_count, st); break;
+    case HISQ_F16: e = phase_launch_HISQ_F16(a, nreal, ds, ctx->sm_count, st); break;
+    case HISQ_BF16: e = phase_launch_HISQ_BF16(a, nreal, ds, ctx->sm_count, st); break;
+    }
+    if (e != cudaSuccess) return cuda_error(ctx, e, "persistent CG phase launch");
+    HISQ_CUDA(ctx, cudaMemcpyAsync(w.h_status, ctx->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    return HISQ_OK;
+}
+
 // r_hi = b - A_precise x_hi ; |r_hi|^2 -> Scalars.last
 int precise_residual(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, int prec)
 {
@@ -523,6 +582,7 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
     // before any capture: the shape (timed on the solver's buffers the first time)
     w.shape = dslash_shape(ctx, ps, w.pv, nrhs, w.p, w.t, w.rbS, st);
     w.fused = o.single_reduction != 0;
+    const int pds = persistent_ds(ctx, w, o, shifts != nullptr);
     const long per_it = w.fused ? 3 : 4; // launches per iteration
     L2Residency l2res;
     const cudaAccessPolicyWindow win = link_window(ctx, ps, o.l2_persist, l2res);
@@ -543,8 +603,8 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
     int since_ru = 0, nru = 0, prev_iters = 0, it_all = 0;
     long kernels = 6 + (o.zero_guess ? 0 : 3); // setup: norms, scalars, conversions (+ residual)
     long dcalls = 0;
-    double dms = 0.0;
-    long dtimed = 0;
+    double dms = 0.0, pms = 0.0;
+    long dtimed = 0, piters = 0, plaunch = 0;
     bool done = false;
     rc = read_scalars(ctx, w, st);
     if (rc) return rc;
@@ -562,15 +622,22 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         const int budget = o.maxiter - (it_all - it_start);
         if (budget <= 0) break;
         int cap = std::min(interval - since_ru, budget);
-        if (!o.use_graph) cap = std::min(cap, ci);
-        k_phase_begin<<<1, 1, 0, st>>>(w.ctl, w.sc, cap);
-        kernels++;
-        // Sampled timing: the phase's first two iterations run as direct launches and the
-        // second one's Dslash pair is timed; queued behind the first, its launches start
-        // back to back on the GPU, so the events hold no host launch gaps.  Taken only when
-        // the phase may run three or more iterations; kept only if both did work.
-        const bool sample = prof && cap >= 3;
-        if (o.use_graph) {
+        if (!o.use_graph && !pds) cap = std::min(cap, ci);
+        // Sampled timing (multi-kernel loop): the phase's first two iterations run as direct
+        // launches and the second one's Dslash pair is timed; queued behind the first, its
+        // launches start back to back on the GPU, so the events hold no host launch gaps.
+        // Taken only when the phase may run three or more iterations; kept only if both did
+        // work.  The persistent kernel is timed as a whole launch instead.
+        const bool sample = prof && cap >= 3 && !pds;
+        if (pds) {
+            // every iteration of the phase in one cooperative launch
+            if (prof) HISQ_CUDA(ctx, cudaEventRecord(w.prof[0], st));
+            if ((rc = launch_persistent_phase(ctx, w, m, cap, pds, o.selftest_wait, st))) return rc;
+            if (prof) HISQ_CUDA(ctx, cudaEventRecord(w.prof[1], st));
+            kernels++;
+        } else if (o.use_graph) {
+            k_phase_begin<<<1, 1, 0, st>>>(w.ctl, w.sc, cap);
+            kernels++;
             if (sample) {
                 if ((rc = launch_iteration(ctx, w, m, st, nullptr, 0))) return rc;
                 if ((rc = launch_iteration(ctx, w, m, st, &w.prof[0], 0))) return rc;
@@ -587,14 +654,32 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             }
             HISQ_CUDA(ctx, cudaGraphLaunch(w.graph, st));
         } else {
+            k_phase_begin<<<1, 1, 0, st>>>(w.ctl, w.sc, cap);
+            kernels++;
             for (int i = 0; i < cap; i++)
                 if ((rc = launch_iteration(ctx, w, m, st, (sample && i == 1) ? &w.prof[0] : nullptr, 0))) return rc;
         }
         if ((rc = read_scalars(ctx, w, st))) return rc;
+        if (pds && w.h_status->error) {
+            cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), st);
+            cudaStreamSynchronize(st);
+            return set_error(ctx, HISQ_EDEVICE, "a grid-barrier wait of the persistent CG kernel ran out");
+        }
         const int executed = w.h_sc[0].it_all - it_all; // iterations the device ran in this phase
         it_all = w.h_sc[0].it_all;
         since_ru += executed;
-        kernels += per_it * executed - (o.use_graph && sample ? 2 * per_it : 0);
+        if (pds) {
+            if (prof) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, w.prof[0], w.prof[1]) == cudaSuccess) {
+                    pms += ms;
+                    piters += executed;
+                    plaunch++;
+                }
+            }
+        } else {
+            kernels += per_it * executed - (o.use_graph && sample ? 2 * per_it : 0);
+        }
         int it = 0;
         bool any_active = false, any_flag = false;
         for (int r = 0; r < nrhs; r++) {
@@ -678,6 +763,10 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         const double dsl = (double)w.Vh * (16.0 * link_bytes(ps, L.nreal) + 2.0 * nrhs * spinor_bytes(w.pv));
         stats->bytes_moved = 2.0 * iters * dsl;
         stats->kernels = kernels;
+        stats->phase_ms = pms;
+        stats->phase_iterations = piters;
+        stats->phase_launches = plaunch;
+        stats->persistent_ds = pds;
     }
     if (!ok) return set_error(ctx, HISQ_ENOTCONVERGED, "hisq_cg: tolerance not reached");
     return HISQ_OK;
@@ -704,6 +793,7 @@ void hisq_solve_opts_default(hisq_solve_opts *o)
     o->single_reduction = 0;
     o->use_graph = 1;
     o->l2_persist = -1;
+    o->persistent = -1;
 }
 
 int hisq_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const hisq_solve_opts *opts,

@@ -84,15 +84,29 @@ __device__ __forceinline__ double acc_norm2(const typename T::Acc &o)
     }
 }
 
-// One work item: the sites of one tile (kDslashBlock threads, DS per site) for the NR
-// right-hand sides whose vectors start at in/out/pv/rv (consecutive right-hand sides
-// a.rhs_bytes apart); geometry g, link store `links`.  Epilogue dot products are added to
-// dots (value j of right-hand side r at dots[r * EpiDots<EPI>::n + j]).
-template <int PL, int PV, int NREAL, int NR, int EPI, int DS>
+// vector load: the read-only path, or (COH) ordinary loads for vectors that other blocks of
+// the same launch write between grid barriers
+template <class T, bool COH>
+__device__ __forceinline__ void vec_load(const char *base, uint32_t s, typename T::Vec &v)
+{
+    if constexpr (COH) T::load_coh(base, s, v);
+    else T::load(base, s, v);
+}
+
+// One work item: the sites of one tile (kDslashBlock threads, DS per site; this thread is
+// number tid of the tile) for the NR right-hand sides whose vectors start at in/out/pv/rv
+// (consecutive right-hand sides a.rhs_bytes apart); geometry g, link store `links`.
+// Epilogue dot products are added to dots (value j of right-hand side r at
+// dots[r * EpiDots<EPI>::n + j]).  With an epilogue, pv, rv and the output are addressed at
+// site s - ebase (ebase = 0: the whole field; else a block's own range, e.g. in shared memory).
+// PF: issue the loads of all four hops of a direction before their products (more requests
+// in flight per thread, more registers).
+template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool COH = false, bool PF = false>
 __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, const char *links, size_t slot_bytes,
                                             double sc0, double sc1, const char *in, char *outp, const char *pvp,
                                             const char *rvp, const double *m4r, uint32_t tile,
-                                            double (&dots)[NR * EpiDots<EPI>::n])
+                                            double (&dots)[NR * EpiDots<EPI>::n], uint32_t tid = threadIdx.x,
+                                            uint32_t ebase = 0)
 {
     constexpr int ND = EpiDots<EPI>::n;
     using T = Prec<PV>;  // vectors and arithmetic
@@ -101,7 +115,7 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
     constexpr bool TWO = (PL == HISQ_F16 || PL == HISQ_BF16 || NREAL == 12);
     constexpr bool SPLIT = T::kSplitDirections;
     constexpr int NMU = 4 / DS;
-    const uint32_t gt = tile * kDslashBlock + threadIdx.x;
+    const uint32_t gt = tile * kDslashBlock + tid;
     const uint32_t u = gt / DS; // site number in launch order
     const int part = (int)(gt % DS);
     const bool live = u < g.Vh;
@@ -131,6 +145,39 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
 #pragma unroll
                 for (int r = 0; r < NR; r++) T::zero(dacc[r]);
             }
+            if constexpr (PF) {
+                // the loads of all four hops first (8 to 12 independent requests per thread in
+                // flight at once), then their products
+                uint32_t w[4][LB / 4];
+                typename T::Vec v[4][NR];
+                bool wrap[4];
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    const int k = h == 0 ? 1 : h == 1 ? -1 : h == 2 ? 3 : -3;
+                    const int type = h >> 1;
+                    const bool back = h & 1;
+                    const uint32_t sn = neighbour(g, c, s, mu, k, wrap[h]);
+                    const int lp = back ? 1 - a.p : a.p;
+                    const char *slot = links + (size_t)((lp * 2 + type) * 4 + mu) * slot_bytes;
+                    load_link_words<LB>(slot, back ? sn : s, w[h], NR > 1 && a.stream_links != 0);
+#pragma unroll
+                    for (int r = 0; r < NR; r++) vec_load<T, COH>(in + (size_t)r * a.rhs_bytes, sn, v[h][r]);
+                }
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    const int type = h >> 1;
+                    const bool back = h & 1;
+                    typename T::Link U;
+                    TL::template unpack<NREAL>(w[h], U);
+                    if constexpr (NREAL == 12) T::rebuild(U, (eta_neg(c, mu) != 0) ^ (mu == 3 && wrap[h]));
+#pragma unroll
+                    for (int r = 0; r < NR; r++) {
+                        typename T::Acc &dst = SPLIT ? dacc[SPLIT ? r : 0] : acc[TWO ? type : 0][r];
+                        if (back) T::template hop<true, true>(dst, U, v[h][r]);
+                        else T::template hop<false, false>(dst, U, v[h][r]);
+                    }
+                }
+            } else {
 #pragma unroll
             for (int h = 0; h < 4; h++) {
                 const int k = h == 0 ? 1 : h == 1 ? -1 : h == 2 ? 3 : -3;
@@ -148,11 +195,12 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
 #pragma unroll
                 for (int r = 0; r < NR; r++) {
                     typename T::Vec v;
-                    T::load(in + (size_t)r * a.rhs_bytes, sn, v);
+                    vec_load<T, COH>(in + (size_t)r * a.rhs_bytes, sn, v);
                     typename T::Acc &dst = SPLIT ? dacc[SPLIT ? r : 0] : acc[TWO ? type : 0][r];
                     if (back) T::template hop<true, true>(dst, U, v);
                     else T::template hop<false, false>(dst, U, v);
                 }
+            }
             }
             if constexpr (SPLIT) {
 #pragma unroll
@@ -184,18 +232,18 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
         for (int r = 0; r < NR; r++) {
             if constexpr (EPI >= 1) {
                 typename T::Vec pv;
-                T::load(pvp + (size_t)r * a.rhs_bytes, s, pv);
+                vec_load<T, COH>(pvp + (size_t)r * a.rhs_bytes, s - ebase, pv);
                 T::mdagm_epilogue(out[r], a.m4 + (m4r ? m4r[r] : 0.0), pv);
                 dots[r * ND] += T::dot(pv, out[r]);
                 if constexpr (EPI == 2) {
                     typename T::Vec rv;
-                    T::load(rvp + (size_t)r * a.rhs_bytes, s, rv);
+                    vec_load<T, COH>(rvp + (size_t)r * a.rhs_bytes, s - ebase, rv);
                     dots[r * ND + 1] += vec_norm2<T>(rv);
                     dots[r * ND + 2] += T::dot(rv, out[r]);
                     dots[r * ND + 3] += acc_norm2<T>(out[r]);
                 }
             }
-            T::store(outp + (size_t)r * a.rhs_bytes, s, out[r]);
+            T::store(outp + (size_t)r * a.rhs_bytes, EPI >= 1 ? s - ebase : s, out[r]);
         }
     }
 }

@@ -72,66 +72,78 @@ struct Reduce {
     int ntotal = 0;             // blocks in the grid (all must arrive before finishing)
 };
 
+// alpha = rr / <p,Ap> from the reduced curvature (FIN_ALPHA)
+__device__ __forceinline__ void fin_alpha(Scalars &S, double total)
+{
+    S.pAp = total;
+    S.astamp = S.it_all;
+    if (S.active && !(total > 0.0 && isfinite(total))) {
+        S.bad = 1;
+        S.active = 0;
+    }
+    S.alpha = S.active ? S.rr / total : 0.0;
+}
+
+// the new |r|^2 has been reduced (FIN_RR): beta, the iteration stamps and the stop/pause flags
+__device__ __forceinline__ void fin_rr(Scalars &S, double total)
+{
+    S.it_all++;
+    if (S.active) {
+        S.iters++;
+        if (!isfinite(total)) {
+            S.bad = 1;
+            S.active = 0;
+            S.beta = 0.0;
+            return;
+        }
+        S.beta = S.rr > 0.0 ? total / S.rr : 0.0;
+        S.rr = total;
+        // the sloppy residual may not run ahead of the true one: at the target, or a
+        // factor delta below the last recomputed residual, the right-hand side pauses
+        // until the host's reliable update (delta2 = 0 for plain FP64 solves)
+        if (total <= S.stop || total < S.delta2 * S.rr_ref) {
+            S.flag = 1;
+            S.active = 0;
+            S.paused = total > S.stop;
+        }
+    }
+    // an inactive right-hand side keeps beta: a reliable update after a pause needs it
+}
+
+// single-reduction step (FIN_AB) once S.pAp = <p,Ap>, S.last_im = |r|^2 (of the stored r) and
+// S.last = <r,Ap> are in place and ApAp = <Ap,Ap>: alpha, then
+// |r - alpha Ap|^2 = |r|^2 - 2 alpha <r,Ap> + alpha^2 <Ap,Ap> and everything FIN_RR does with it
+__device__ __forceinline__ void fin_ab(Scalars &S, double ApAp)
+{
+    if (S.active && isfinite(S.last_im)) S.rr = S.last_im;
+    const double pAp = S.pAp;
+    S.astamp = S.it_all;
+    if (S.active && !(pAp > 0.0 && isfinite(pAp))) {
+        S.bad = 1;
+        S.active = 0;
+    }
+    S.alpha = S.active ? S.rr / pAp : 0.0;
+    double rr = S.rr;
+    if (S.active) {
+        rr = S.rr - 2.0 * S.alpha * S.last + S.alpha * S.alpha * ApAp;
+        if (isfinite(rr) && rr < 0.0) rr = 0.0; // rounding: the residual has vanished
+    }
+    fin_rr(S, rr);
+}
+
 __device__ __forceinline__ void finish_value(const Reduce &R, int v, double total)
 {
     Scalars &S = R.sc[R.op == FIN_CDOT ? (v >> 1) : R.op == FIN_AB ? (v >> 2) : v];
-    int op = R.op;
-    if (op == FIN_AB) {
+    switch (R.op) {
+    case FIN_AB:
         switch (v & 3) {
         case 0: S.pAp = total; return;     // <p, Ap>
         case 1: S.last_im = total; return; // |r|^2 of the stored r
         case 2: S.last = total; return;    // <r, Ap>
-        default: break;                    // <Ap, Ap>: finish
+        default: fin_ab(S, total); return; // <Ap, Ap>: finish
         }
-        if (S.active && isfinite(S.last_im)) S.rr = S.last_im;
-        const double pAp = S.pAp;
-        S.astamp = S.it_all;
-        if (S.active && !(pAp > 0.0 && isfinite(pAp))) {
-            S.bad = 1;
-            S.active = 0;
-        }
-        S.alpha = S.active ? S.rr / pAp : 0.0;
-        double rr = S.rr;
-        if (S.active) {
-            rr = S.rr - 2.0 * S.alpha * S.last + S.alpha * S.alpha * total;
-            if (isfinite(rr) && rr < 0.0) rr = 0.0; // rounding: the residual has vanished
-        }
-        total = rr;
-        op = FIN_RR;
-    }
-    switch (op) {
-    case FIN_ALPHA:
-        S.pAp = total;
-        S.astamp = S.it_all;
-        if (S.active && !(total > 0.0 && isfinite(total))) {
-            S.bad = 1;
-            S.active = 0;
-        }
-        S.alpha = S.active ? S.rr / total : 0.0;
-        break;
-    case FIN_RR:
-        S.it_all++;
-        if (S.active) {
-            S.iters++;
-            if (!isfinite(total)) {
-                S.bad = 1;
-                S.active = 0;
-                S.beta = 0.0;
-                break;
-            }
-            S.beta = S.rr > 0.0 ? total / S.rr : 0.0;
-            S.rr = total;
-            // the sloppy residual may not run ahead of the true one: at the target, or a
-            // factor delta below the last recomputed residual, the right-hand side pauses
-            // until the host's reliable update (delta2 = 0 for plain FP64 solves)
-            if (total <= S.stop || total < S.delta2 * S.rr_ref) {
-                S.flag = 1;
-                S.active = 0;
-                S.paused = total > S.stop;
-            }
-        }
-        // an inactive right-hand side keeps beta: a reliable update after a pause needs it
-        break;
+    case FIN_ALPHA: fin_alpha(S, total); break;
+    case FIN_RR: fin_rr(S, total); break;
     case FIN_CDOT:
         if (v & 1) R.sc[v >> 1].last_im = total;
         else R.sc[v >> 1].last = total;

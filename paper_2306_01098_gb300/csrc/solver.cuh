@@ -21,6 +21,8 @@ struct SolverWork {
     double *partials = nullptr;
     unsigned *counter = nullptr;
     LoopCtl *ctl = nullptr;  // device-side loop control
+    void *phase_slots = nullptr; // arrival records of the persistent phase kernel (kPhaseMaxBlocks)
+    DevStatus *h_status = nullptr; // pinned host copy of the device error flag
     double *shift_buf = nullptr, *h_shift = nullptr; // per right-hand side shifts (device, pinned host)
     const double *shift = nullptr;                   // shift_buf when shifts are in use
     std::vector<double> shift_key, graph_shift;      // shifts the loop graph was captured with

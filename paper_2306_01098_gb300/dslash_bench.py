@@ -1,6 +1,10 @@
 """Dslash throughput on internal-layout fields: GB/s against the HBM roofline, TFLOP/s.
 
   python -m paper_2306_01098_gb300.dslash_bench --dims 64,64,64,16 --prec f64x,f32 --nrhs 1,4 [--comp 12]
+  python -m paper_2306_01098_gb300.dslash_bench --prec f32 --nrhs 16 --sweep    # every launch shape
+
+The timed repetitions run inside an NVTX range named "timed", so that a profiler can be told
+to capture only launches with the autotuned (or pinned) shape.
 
 Algorithmic bytes per application (Sec. 5.1 accounting with perfect neighbour reuse):
   Vh * (16 * link_bytes + nrhs * 2 * spinor_bytes)
@@ -27,12 +31,36 @@ def alg_bytes(Vh, prec, nreal, nrhs):
     return Vh * (16 * nreal * LINK_REAL_BYTES[prec] + nrhs * 2 * SPINOR_BYTES[prec])
 
 
+def hbm_peak():
+    """Measured copy bandwidth of this GPU model (GB/s) from MEASURED_PEAKS.json, else the
+    6800 GB/s of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+def shapes(prec, nrhs, zt_ok=True):
+    """Every (n_inner, threads per site, site order) launch shape the autotuner considers."""
+    cap = 4 if prec in ("f64", "f64x") else 8
+    out = []
+    for order in ((0, 1) if zt_ok else (0,)):
+        nr = 1
+        while nr <= cap:
+            if nrhs % nr == 0:
+                out.extend((nr, ds, order) for ds in (1, 2, 4))
+            nr *= 2
+    return out
+
+
 def measure(dims=(64, 64, 64, 16), precs=("f64", "f64x", "f32", "f16"), nrhs_list=(1,), comp=18, reps=10,
-            hbm_gbs=6763.3, seed=1002):
+            hbm_gbs=None, seed=1002, shape=None, sweep=False):
     import torch
 
     from hisq_inputs import fields
     from paper_2306_01098_gb300 import hisq
+    hbm_gbs = hbm_gbs or hbm_peak()
     ps = [NAMES[p] for p in precs if not (p == "f64x" and comp == 12)]
     fat, lng = fields.recipe_links(dims, 0.3, seed, device="cuda")
     ctx = hisq.Context(dims, fat, lng, precs=tuple(ps), compression={p: comp for p in ps})
@@ -40,27 +68,37 @@ def measure(dims=(64, 64, 64, 16), precs=("f64", "f64x", "f32", "f16"), nrhs_lis
     torch.cuda.empty_cache()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     out = []
+    zt_ok = dims[3] < dims[2] and (dims[0] // 2 * dims[1]) % 32 == 0
     for p in ps:
         for nrhs in nrhs_list:
             fi, fo = ctx.field(p, nrhs), ctx.field(p, nrhs)
             fi.load(fields.gaussian_source(dims, 7, nrhs, device="cuda"))
-            for _ in range(3):
-                ctx.dslash_field(0, fi, fo)
-            torch.cuda.synchronize()
-            ts = []
-            for it in range(reps):
-                flush.add_(1.0)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                ctx.dslash_field(it & 1, fi, fo)
-                e1.record()
+            pinned = shapes(hisq.PREC_NAMES[p], nrhs, zt_ok) if sweep else [shape]
+            for sh in pinned:
+                if sh is not None:
+                    ctx.tune_set(p, p, nrhs, *sh)
+                for _ in range(3):
+                    ctx.dslash_field(0, fi, fo)
                 torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            ms = sorted(ts)[len(ts) // 2]
-            b = alg_bytes(ctx.Vh, p, comp, nrhs)
-            out.append({"prec": hisq.PREC_NAMES[p], "nreal": comp, "nrhs": nrhs, "us": ms * 1e3,
-                        "gbs": b / ms / 1e6, "frac_hbm": b / ms / 1e6 / hbm_gbs,
-                        "tflops": 1146 * ctx.Vh * nrhs / ms / 1e9, "bytes": b})
+                ts = []
+                torch.cuda.nvtx.range_push("timed")
+                for it in range(reps):
+                    flush.add_(1.0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    ctx.dslash_field(it & 1, fi, fo)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                torch.cuda.nvtx.range_pop()
+                ms = sorted(ts)[len(ts) // 2]
+                b = alg_bytes(ctx.Vh, p, comp, nrhs)
+                row = {"prec": hisq.PREC_NAMES[p], "nreal": comp, "nrhs": nrhs, "us": ms * 1e3,
+                       "gbs": b / ms / 1e6, "frac_hbm": b / ms / 1e6 / hbm_gbs,
+                       "tflops": 1146 * ctx.Vh * nrhs / ms / 1e9, "bytes": b}
+                if sh is not None:
+                    row["shape"] = {"n_inner": sh[0], "threads_per_site": sh[1], "site_order": sh[2]}
+                out.append(row)
             fi.close()
             fo.close()
     ctx.close()
@@ -74,9 +112,12 @@ def main():
     ap.add_argument("--nrhs", default="1")
     ap.add_argument("--comp", type=int, default=18)
     ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--shape", default=None, help="n_inner,threads_per_site,site_order instead of the autotuner")
+    ap.add_argument("--sweep", action="store_true", help="time every launch shape")
     a = ap.parse_args()
+    shape = tuple(int(v) for v in a.shape.split(",")) if a.shape else None
     rows = measure(tuple(int(v) for v in a.dims.split(",")), tuple(a.prec.split(",")),
-                   tuple(int(v) for v in a.nrhs.split(",")), a.comp, a.reps)
+                   tuple(int(v) for v in a.nrhs.split(",")), a.comp, a.reps, shape=shape, sweep=a.sweep)
     for r in rows:
         print(json.dumps(r))
 

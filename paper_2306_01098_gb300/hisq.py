@@ -40,7 +40,8 @@ class SolveOpts(ctypes.Structure):
                 ("reliable_delta", ctypes.c_double), ("zero_guess", ctypes.c_int),
                 ("host_buffers", ctypes.c_int), ("check_interval", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("profile", ctypes.c_int), ("l2_persist", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("single_reduction", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("single_reduction", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("selftest_wait", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -48,7 +49,9 @@ class Stats(ctypes.Structure):
                 ("true_residual", ctypes.c_double), ("iterated_residual", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("dslash_calls", ctypes.c_long),
                 ("dslash_ms", ctypes.c_double), ("dslash_timed", ctypes.c_long),
-                ("bytes_moved", ctypes.c_double), ("kernels", ctypes.c_long)]
+                ("bytes_moved", ctypes.c_double), ("kernels", ctypes.c_long), ("phase_ms", ctypes.c_double),
+                ("phase_iterations", ctypes.c_long), ("phase_launches", ctypes.c_long),
+                ("persistent_ds", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -103,7 +103,7 @@ def test_graph_and_direct_launch_agree():
     for g in (0, 1):
         x = torch.zeros_like(b)
         rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, use_graph=g, check_interval=20,
-                        reliable_interval=100)
+                        reliable_interval=100, persistent=0)
         assert rc == hisq.OK
         xs.append((x.cpu(), st.iterations))
     assert xs[0][1] == xs[1][1]
@@ -115,7 +115,8 @@ def test_profiled_solve_counts_dslash_launches():
     ctx, fat, lng = setup(dims, 0.5, 1012)
     b = fields.gaussian_source(dims, 2171)[0].cuda()
     x = torch.zeros_like(b)
-    rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, profile=1, check_interval=10)
+    rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, profile=1, check_interval=10,
+                    persistent=0)
     assert rc == hisq.OK
     # the two Dslash launches of the second iteration of every phase of three or more
     # iterations are timed
@@ -205,7 +206,7 @@ def test_single_and_two_reduction_iterations_agree(sloppy, nrhs):
         x = torch.zeros_like(b).cuda()
         res = torch.zeros(nrhs, dtype=torch.float64)
         rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=sloppy, prec_precise=hisq.F64, reliable_delta=0.01,
-                        single_reduction=single, residuals=res)
+                        single_reduction=single, residuals=res, persistent=0)
         assert rc == hisq.OK
         for k in range(nrhs):
             assert true_res(dims, fat, lng, m, b[k].numpy(), x[k].cpu().numpy()) <= 1e-10
@@ -229,7 +230,7 @@ def test_pause_inside_timed_iterations_ends_device_loop(single):
     b = fields.gaussian_source(dims, 2170)[0]
     x = torch.zeros_like(b).cuda()
     rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, reliable_delta=0.5,
-                    profile=1, single_reduction=single)
+                    profile=1, single_reduction=single, persistent=0)
     assert rc == hisq.OK
     assert true_res(dims, fat, lng, m, b.numpy(), x.cpu().numpy()) <= 1e-10
     print(f"single_reduction {single}: {st.iterations} iterations, {st.reliable_updates} reliable updates")
@@ -287,3 +288,83 @@ def test_condensate_estimator():
     print(f"condensate: estimate {pbp:.6f} +- {err:.6f}, exact {exact:.6f}")
     assert abs(pbp - exact) <= 5 * err
     ctx.close()
+
+
+# ---------------------------------------------------------------- persistent phase kernel
+@pytest.mark.parametrize("sloppy,nreal,ds", [(hisq.F16, 18, 1), (hisq.F16, 18, 2), (hisq.F16, 18, 4), (hisq.F32, 18, 2),
+                                             (hisq.BF16, 18, 4), (hisq.F16, 12, 2), (hisq.BF16, 12, 1)])
+def test_persistent_phase_cg(sloppy, nreal, ds):
+    # every sloppy iteration between two reliable updates in one cooperative launch (one block
+    # per SM, bounded grid barriers), on a lattice whose half volume (2880) is no multiple of
+    # the 128-site tile; the short reliable-update interval makes phases end at their cap
+    # (p left to the host) as well as on the delta trigger
+    dims, m = (6, 8, 10, 12), 0.02
+    ctx, fat, lng = setup(dims, 0.5, 1020, precs=(hisq.F64, sloppy), comp={sloppy: nreal})
+    b = fields.gaussian_source(dims, 2190)[0]
+    x = torch.full_like(b, float("nan")).cuda()
+    rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=sloppy, prec_precise=hisq.F64, reliable_interval=30,
+                    persistent=ds)
+    assert rc == hisq.OK, st.as_dict()
+    assert st.persistent_ds == ds
+    res = true_res(dims, fat, lng, m, b.numpy(), x.cpu().numpy())
+    assert res <= 1e-10
+    # the recurrences of the multi-kernel single-reduction loop, summed in another order
+    x2 = torch.zeros_like(b).cuda()
+    rc2, st2 = ctx.cg(m, b.cuda(), x2, tol=1e-10, prec_sloppy=sloppy, prec_precise=hisq.F64, reliable_interval=30,
+                      persistent=0, single_reduction=1)
+    assert rc2 == hisq.OK and st2.persistent_ds == 0
+    print(f"persistent {hisq.PREC_NAMES[sloppy]}/{nreal} ds {ds}: {st.iterations} iterations "
+          f"({st.reliable_updates} reliable updates), multi-kernel {st2.iterations}; true residual {res:.2e}")
+    assert abs(st.iterations - st2.iterations) <= max(3, st2.iterations // 20)
+
+
+def test_persistent_phase_deterministic_and_timed():
+    dims, m = (8, 8, 8, 8), 0.05
+    ctx, fat, lng = setup(dims, 0.5, 1012)
+    b = fields.gaussian_source(dims, 2172)[0].cuda()
+    out = []
+    for _ in range(2):
+        x = torch.zeros_like(b)
+        rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F16, prec_precise=hisq.F64, profile=1, persistent=2)
+        assert rc == hisq.OK
+        out.append((x.cpu(), st.iterations))
+        # every phase is one timed launch; its iterations add up to the solve's
+        assert st.phase_iterations == st.iterations and st.phase_ms > 0 and st.dslash_timed == 0
+    assert out[0][1] == out[1][1]
+    assert torch.equal(out[0][0], out[1][0])     # fixed partial order in every block: bitwise
+
+
+def test_persistent_phase_bench_workload():
+    # the 32^3 x 8 bench workload (eps 0.5, m 0.01): 16-bit links with 18 and 12 reals
+    dims, m = (32, 32, 32, 8), 0.01
+    fat, lng = fields.recipe_links(dims, 0.5, 1001, device="cuda")
+    b = fields.gaussian_source(dims, 2001)[0]
+    fh, lh = fat.cpu().numpy(), lng.cpu().numpy()
+    for nreal in (18, 12):
+        ctx = hisq.Context(dims, fat, lng, precs=(hisq.F64, hisq.F16), compression={hisq.F16: nreal})
+        x = torch.zeros_like(b).cuda()
+        rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=hisq.F16, prec_precise=hisq.F64,
+                        reliable_delta=0.01)
+        assert rc == hisq.OK and st.persistent_ds > 0
+        res = true_res(dims, fh, lh, m, b.numpy(), x.cpu().numpy())
+        print(f"32^3x8 persistent F16/{nreal}: {st.iterations} iterations, {st.reliable_updates} reliable updates, "
+              f"true residual {res:.2e}")
+        assert res <= 1e-10
+        ctx.close()
+
+
+def test_persistent_barrier_wait_is_bounded():
+    # one block leaves the first launch without arriving at its first grid barrier: every
+    # other block's wait runs out after 1 ms, raises the device error flag and ends the
+    # launch; the solve reports HISQ_EDEVICE and the next solve on the context converges
+    dims, m = (8, 8, 8, 8), 0.05
+    ctx, fat, lng = setup(dims, 0.5, 1012)
+    b = fields.gaussian_source(dims, 2173)[0].cuda()
+    with pytest.raises(hisq.HisqError) as err:
+        ctx.cg(m, b, torch.zeros_like(b), tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, persistent=2,
+               selftest_wait=1)
+    assert err.value.code == hisq.EDEVICE
+    x = torch.zeros_like(b)
+    rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, persistent=2)
+    assert rc == hisq.OK
+    assert true_res(dims, fat, lng, m, b.cpu().numpy(), x.cpu().numpy()) <= 1e-10
