@@ -225,6 +225,82 @@ def traffic_for(kernel_key: str):
         return None
 
 
+def workload_configs(hbm):
+    """The other workloads of the benchmark definition, measured after the timed region (one
+    GPU, rank 0); every solve to a true FP64 residual <= 1e-10.  Returns a dict for the line.
+      64^3x16 (eps 0.3, m 0.01): FP32 Dslash at nrhs 1/4/8/16 (HBM-streaming, L2 flushed),
+        mixed CG (FP32 sloppy, FP64 reliable updates) at nrhs 1 and 8 against plain FP64 CG,
+        14-shift multi-shift CG (FP32 sloppy), and the 32 uneven lattices batched vs one by one;
+      32^3x8 learned preconditioner (eps 0.5, m 0.005): 2000 training pairs, 4 epochs, flexible
+        CG with the network against plain and mixed CG on 10 held-out sources;
+      96^3x24 (eps 0.3, m 0.01, 12-real 16-bit links): Dslash HBM fraction and the 14-shift
+        mixed multi-shift solve."""
+    import torch
+
+    from hisq_inputs import fields, workloads
+    from paper_2306_01098_gb300 import dslash_bench, hisq, precond_bench, solver_bench
+    out = {}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t0), r
+
+    # ---- 64^3 x 16
+    w = workloads.BATCH_64x16
+    c = {"regime": "HBM-streaming (link store 2.4 GB FP32 > L2)"}
+    c["dslash_f32"] = dslash_bench.measure(w.dims, ("f32",), (1, 4, 8, 16), 18, reps=5, hbm_gbs=hbm, seed=w.link_seed)
+    torch.cuda.empty_cache()
+    fat, lng = fields.recipe_links(w.dims, w.eps, w.link_seed, device="cuda")
+    ctx = hisq.Context(w.dims, fat, lng, precs=(hisq.F64, hisq.F32))
+    del fat, lng
+    torch.cuda.empty_cache()
+    b1 = fields.gaussian_source(w.dims, w.source_seed, 1, device="cuda")
+    x1 = torch.zeros_like(b1)
+    ms64, (rc, st) = timed(lambda: ctx.cg(w.mass, b1, x1.zero_(), tol=w.tol, prec_sloppy=hisq.F64))
+    c["fp64_cg"] = {"nrhs": 1, "ms": ms64, "iterations": st.iterations, "true_residual": st.true_residual}
+    c["mixed_cg_f32"] = []
+    for nrhs in (1, 8):
+        b = fields.gaussian_source(w.dims, w.source_seed, nrhs, device="cuda")
+        x = torch.zeros_like(b)
+        res = torch.zeros(nrhs, dtype=torch.float64)
+        solve = lambda: ctx.cg(w.mass, b, x.zero_(), tol=w.tol, prec_sloppy=hisq.F32, prec_precise=hisq.F64,
+                               reliable_delta=0.01, residuals=res)
+        solve()
+        ms, (rc, st) = timed(solve)
+        c["mixed_cg_f32"].append({"nrhs": nrhs, "ms": ms, "ms_per_rhs": ms / nrhs, "iterations": st.iterations,
+                                  "reliable_updates": st.reliable_updates, "max_true_residual": float(res.max()),
+                                  "speedup_per_rhs_vs_fp64_cg": ms64 / (ms / nrhs), "converged": rc == hisq.OK})
+        del b, x
+    sig = list(w.shifts)
+    xs = [torch.zeros_like(b1[0]) for _ in sig]
+    res = torch.zeros(len(sig), dtype=torch.float64)
+    ms, (rc, st) = timed(lambda: ctx.multishift_cg(w.mass, sig, b1[0].contiguous(), xs, tol=[w.tol] * len(sig),
+                                                   prec_sloppy=hisq.F32, prec_precise=hisq.F64, reliable_delta=0.01,
+                                                   residuals=res))
+    c["multishift_14_f32"] = {"ms": ms, "iterations": st.iterations, "max_true_residual": float(res.max()),
+                              "converged": rc == hisq.OK}
+    ctx.close()
+    del xs, b1, x1
+    torch.cuda.empty_cache()
+    c["uneven_32_lattices"] = solver_bench.uneven(reps=1)
+    out["config_64x64x64x16"] = c
+    torch.cuda.empty_cache()
+
+    # ---- learned preconditioner, 32^3 x 8, m 0.005
+    rows = precond_bench.run(pairs=2000, epochs=4, test=10)
+    out["config_learned_32x32x32x8"] = {"regime": "L2-resident (16-bit links 75 MB)", "rows": rows}
+    torch.cuda.empty_cache()
+
+    # ---- 96^3 x 24, 12-real 16-bit links
+    rows = solver_bench.large(reps=1)
+    out["config_96x96x96x24"] = {"regime": "HBM-streaming (16-bit 12-real link store 4.1 GB)", "rows": rows}
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -361,6 +437,11 @@ def run_ours(args, world, rank, local):
         from paper_2306_01098_gb300 import dslash_bench
         table = dslash_bench.measure((64, 64, 64, 16), ("f64", "f64x", "f32", "f16"), (1,), 18, hbm_gbs=hbm)
     cb = oracle_sample(args.cpu_seconds, st64.iterations) if not args.no_cpu_baseline else None
+    configs = None
+    if world == 1 and not args.no_configs:
+        del ctx
+        torch.cuda.empty_cache()
+        configs = workload_configs(hbm)
     line = {
         "metric": METRIC, "value": ms_per_solve, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_solve, "higher_is_better": False, "scaling": "weak",
@@ -390,6 +471,7 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": int(b.numel() * 16)},
         "gpu_launches": int(sum(s.kernels for s in stats)) + args.steps,
         "clocks": clocks,
+        "workload_configs": configs,
     }
     print(json.dumps(line), flush=True)
 
@@ -412,6 +494,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dslash-table", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the 64^3x16, learned and 96^3x24 workloads")
     ap.add_argument("--fp64-reps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--oracle-table", action="store_true",

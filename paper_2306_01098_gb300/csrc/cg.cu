@@ -460,7 +460,7 @@ static int persistent_ds(hisq_ctx *ctx, const SolverWork &w, const hisq_solve_op
     }
     // the block's x, r, p and Ap must fit in shared memory
     if (phase_chunk(w.Vh, ctx->sm_count) == 0) return 0;
-    if (o.persistent >= 1 && o.persistent <= 4) return o.persistent;
+    if (o.persistent >= 1 && o.persistent <= 5) return o.persistent;
     return 2;
 }
 
@@ -629,12 +629,28 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         // Taken only when the phase may run three or more iterations; kept only if both did
         // work.  The persistent kernel is timed as a whole launch instead.
         const bool sample = prof && cap >= 3 && !pds;
+        // reliable update: x_hi += x_lo, r_hi = b - A_precise x_hi, scalars, r = sloppy(r_hi)
+        auto queue_ru = [&]() -> int {
+            dispatch(w.pv, [&](auto T) { decltype(T)::accum_hi(w, st); });
+            int e = precise_residual(ctx, w, m, st, w.pp);
+            if (e) return e;
+            k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_RU, tol2, delta2);
+            dispatch(w.pv, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
+            kernels += 5 + (w.pp == HISQ_F64X ? 1 : 0);
+            return HISQ_OK;
+        };
+        bool ru_queued = false;
         if (pds) {
             // every iteration of the phase in one cooperative launch
             if (prof) HISQ_CUDA(ctx, cudaEventRecord(w.prof[0], st));
             if ((rc = launch_persistent_phase(ctx, w, m, cap, pds, o.selftest_wait, st))) return rc;
             if (prof) HISQ_CUDA(ctx, cudaEventRecord(w.prof[1], st));
             kernels++;
+            // a persistent phase always ends in a reliable update (a pause, convergence, the
+            // interval cap or the iteration budget): queue it before looking at the scalars,
+            // which the update leaves as the phase left them apart from the residual state
+            if ((rc = queue_ru())) return rc;
+            ru_queued = true;
         } else if (o.use_graph) {
             k_phase_begin<<<1, 1, 0, st>>>(w.ctl, w.sc, cap);
             kernels++;
@@ -700,15 +716,13 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             }
         }
         const bool last = it_all - it_start >= o.maxiter;
-        if (any_flag || since_ru >= interval || !any_active || last) {
-            dispatch(w.pv, [&](auto T) { decltype(T)::accum_hi(w, st); });
-            if ((rc = precise_residual(ctx, w, m, st, w.pp))) return rc;
-            k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_RU, tol2, delta2);
-            dispatch(w.pv, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
-            kernels += 5 + (w.pp == HISQ_F64X ? 1 : 0);
+        if (ru_queued || any_flag || since_ru >= interval || !any_active || last) {
+            if (!ru_queued) {
+                if ((rc = queue_ru())) return rc;
+                if ((rc = read_scalars(ctx, w, st))) return rc;
+            }
             nru++;
             since_ru = 0;
-            if ((rc = read_scalars(ctx, w, st))) return rc;
             bool any = false;
             for (int r = 0; r < nrhs; r++) any |= w.h_sc[r].active != 0;
             if (!any && w.pp != HISQ_F64 && ctx->links[HISQ_F64].built) {

@@ -24,13 +24,15 @@
 // device error flag and ends the launch early; the host turns the flag into HISQ_EDEVICE.
 #pragma once
 
+#include <cstddef>
+
 #include "blas.cuh"
 #include "dslash_kernel.cuh"
 
 namespace hisq {
 
 // Launch shapes (threads per block NT, prefetch PF), chosen by code:
-//   1: NT 1024     2: NT 512, PF     3: NT 896, PF     4: NT 1024, PF
+//   1: NT 1024     2: NT 512, PF     3: NT 896, PF     4: NT 1024, PF     5: NT 448, PF
 // PF issues the loads of all four hops of a direction before their products; fewer threads
 // per block leave it the registers that needs (a block of NT threads walks its c sites in
 // ceil(c / NT) passes).
@@ -38,12 +40,13 @@ namespace hisq {
 // Arrival record of one block (one 64-byte line): the number of grid barriers it has passed
 // and, at the barrier after the normal operator, its partial sums of the four dot products.
 struct PhaseSlot {
+    double part[4]; // first: 16-byte aligned for the paired loads that copy it
     unsigned gen;
     unsigned pad;
-    double part[4];
     double pad2[3];
 };
 static_assert(sizeof(PhaseSlot) == 64, "one arrival record per 64-byte line");
+static_assert(offsetof(PhaseSlot, part) % 16 == 0, "partial sums are read as 16-byte pairs");
 constexpr int kPhaseMaxBlocks = 1024;
 // shared memory per owned site: x, r, p, Ap (FP32 records)
 constexpr int kPhaseSmemPerSite = 4 * 24;
@@ -70,6 +73,13 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
     return v;
 }
 
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -85,10 +95,13 @@ __device__ __forceinline__ unsigned long long phase_clock_ns()
 // Grid-wide barrier number g of a cooperative launch (every block resident).  After the
 // block's threads meet, thread 0 writes the block's partial sums (if any) and releases g in
 // the block's own record; the release orders every write the block made before the meeting.
-// Thread i < gridDim.x of every block then waits until record i shows g (acquire), at most
-// limit_ns.  Returns false, with the device error flag raised, if a wait ran out.
+// Thread i < gridDim.x of every block then waits until record i shows g (relaxed polling,
+// then one acquire fence by the same thread), at most limit_ns.  Returns false, with the
+// device error flag raised, if a wait ran out.
+// With spart (shared memory, [4][gridDim.x]), the thread that waited for record i also copies
+// that block's partial sums there, so all of them arrive in one parallel round trip.
 __device__ __forceinline__ bool grid_barrier(PhaseSlot *slots, unsigned g, const double *mine, DevStatus *st,
-                                            unsigned long long limit_ns)
+                                            unsigned long long limit_ns, double *spart = nullptr)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -101,7 +114,7 @@ __device__ __forceinline__ bool grid_barrier(PhaseSlot *slots, unsigned g, const
         const unsigned *f = &slots[threadIdx.x].gen;
         unsigned long long t0 = 0;
         int n = 0;
-        while ((int)(ld_acquire_gpu(f) - g) < 0) {
+        while ((int)(ld_relaxed_gpu(f) - g) < 0) {
             if (++n < 128) continue;
             n = 0;
             const unsigned long long t = phase_clock_ns();
@@ -110,6 +123,15 @@ __device__ __forceinline__ bool grid_barrier(PhaseSlot *slots, unsigned g, const
                 good = 0;
                 break;
             }
+        }
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        if (spart && good) {
+            const double2 *q = reinterpret_cast<const double2 *>(slots[threadIdx.x].part);
+            const double2 a0 = __ldcg(q), a1 = __ldcg(q + 1);
+            spart[threadIdx.x] = a0.x;
+            spart[gridDim.x + threadIdx.x] = a0.y;
+            spart[2 * gridDim.x + threadIdx.x] = a1.x;
+            spart[3 * gridDim.x + threadIdx.x] = a1.y;
         }
     }
     good = __syncthreads_and(good);
@@ -122,7 +144,7 @@ __device__ __forceinline__ bool grid_barrier(PhaseSlot *slots, unsigned g, const
 
 // PL: sloppy link storage (F32, F16, BF16) with NREAL reals; vectors FP32; NT threads per
 // block; PF prefetch of a direction's four hops.  Dynamic shared memory: x, r, p, Ap of the
-// block's sites (a.chunk records of 24 bytes each).
+// block's sites (a.chunk records of 24 bytes each), then [4][gridDim.x] partial sums.
 template <int PL, int NREAL, int NT, bool PF>
 __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
 {
@@ -136,6 +158,7 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
     const uint32_t cbeg = min(a.Vh, blockIdx.x * a.chunk), cend = min(a.Vh, cbeg + a.chunk);
     char *sx = phase_smem, *sr = sx + (size_t)a.chunk * 24, *sp = sr + (size_t)a.chunk * 24;
     char *sAp = sp + (size_t)a.chunk * 24;
+    double *spart = reinterpret_cast<double *>(sAp + (size_t)a.chunk * 24); // [4][gridDim.x]
     for (uint32_t s = cbeg + threadIdx.x; s < cend; s += NT) {
         typename B::Vec v;
         T::load_coh(a.x, s, v);
@@ -169,15 +192,15 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
                                                                     a.deo.scale[0], a.deo.scale[1], a.deo.in, sAp, sp,
                                                                     sr, nullptr, 0u, d, s, cbeg);
             block_sum_multi<4>(d);
-            if (!(ok = grid_barrier(a.slots, ++g, d, a.status, a.wait_ns))) break;
+            if (!(ok = grid_barrier(a.slots, ++g, d, a.status, a.wait_ns, spart))) break;
         }
         // the same totals in every block: lane i sums the partials of blocks i, i + 32, ...
-        // then a fixed tree
+        // (copied to shared memory by the barrier) then a fixed tree
         if (threadIdx.x < 32) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 double acc = 0.0;
-                for (uint32_t i = threadIdx.x; i < G; i += 32) acc += __ldcg(&a.slots[i].part[j]);
+                for (uint32_t i = threadIdx.x; i < G; i += 32) acc += spart[j * G + i];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
                 if (threadIdx.x == 0) tot[j] = acc;
@@ -239,7 +262,7 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
 inline uint32_t phase_chunk(uint32_t Vh, int sms)
 {
     const uint32_t c = ((Vh + (uint32_t)sms - 1) / (uint32_t)sms + 31u) & ~31u;
-    return (size_t)c * kPhaseSmemPerSite <= (size_t)kPhaseMaxSmem ? c : 0u;
+    return (size_t)c * kPhaseSmemPerSite + 4 * sizeof(double) * (size_t)sms <= (size_t)kPhaseMaxSmem ? c : 0u;
 }
 
 // one block per SM; every block polls every record, so blocks <= NT
@@ -250,7 +273,7 @@ static cudaError_t launch_phase_t(const PhaseArgs &a0, int sms, cudaStream_t st)
     PhaseArgs a = a0;
     a.chunk = phase_chunk(a.Vh, sms);
     if (a.chunk == 0 || sms > NT || sms > kPhaseMaxBlocks) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)a.chunk * kPhaseSmemPerSite;
+    const size_t smem = (size_t)a.chunk * kPhaseSmemPerSite + 4 * sizeof(double) * (size_t)sms;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_cg_phase<PL, NREAL, NT, PF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kPhaseMaxSmem);
@@ -282,6 +305,7 @@ cudaError_t launch_phase_shape(const PhaseArgs &a, int shape, int sms, cudaStrea
     case 2: return launch_phase_t<PL, NREAL, 512, true>(a, sms, st);
     case 3: return launch_phase_t<PL, NREAL, 896, true>(a, sms, st);
     case 4: return launch_phase_t<PL, NREAL, 1024, true>(a, sms, st);
+    case 5: return launch_phase_t<PL, NREAL, 448, true>(a, sms, st);
     }
     return cudaErrorInvalidValue;
 }
