@@ -415,6 +415,42 @@ int hisq_net_load(hisq_ctx *ctx, const char *path, hisq_net **net);
 int hisq_fcg(hisq_ctx *ctx, double m, hisq_net *net, const double *b, double *x, const hisq_solve_opts *opts,
              hisq_stats *stats);
 
+/* ------------------------------------------------------------------ domain decomposition */
+/* The Dslash on one time slab of a lattice cut into slabs (Sec. 4, "Communication": each
+ * sub-lattice keeps its bulk and a halo of the neighbours' boundary sites, exchanged once per
+ * operator application).  Slab [t0, t0 + lt) of the global lattice gdims = (Nx, Ny, Nz, Nt),
+ * t0 and lt even, lt >= 4, t0 + lt <= Nt.  Fields on the slab use the slab's own even-odd
+ * order (Sec. 4.3 on dims Nx, Ny, Nz, lt): [Vh_slab][3] complex128, Vh_slab = Nx Ny Nz lt / 2;
+ * a site's parity there equals its global parity.  The stencil reaches three slices across a
+ * cut, so D_{p,1-p} on the slab needs the parity 1-p field on the three slices below t0
+ * (halo_lo: global t0-3, t0-2, t0-1, modulo Nt) and on t0+lt .. t0+lt+2 (halo_hi): two
+ * buffers of 3 F records, F = Nx Ny Nz / 2, slice after slice, the record of (x, y, z) at
+ * face index (x + Nx (y + Ny z)) / 2 within its slice.  The slab below sends its three top
+ * slices, the slab above its three bottom slices (hisq_dd_pack); moving them between
+ * processes or GPUs (NCCL send/recv, a device copy) is the caller's step. */
+typedef struct hisq_dd hisq_dd;
+/* fat, lng: the GLOBAL canonical [4][V][3][3] links WITHOUT phases (host or device per
+ * opts->links_on_device; opts->links_phased must be 0; opts->device selects the GPU).  The
+ * library copies the slab's links and the time-direction links of the three slices below
+ * it, folds in the MILC phases and the antiperiodic time boundary by global position, and
+ * keeps them in FP64; the caller keeps ownership.  HISQ_EINVAL for bad dims or slab bounds. */
+int hisq_dd_create(hisq_dd **dd, const int gdims[4], int t0, int lt, const double *fat, const double *lng,
+                   const hisq_opts *opts);
+void hisq_dd_destroy(hisq_dd *dd);
+const char *hisq_dd_last_error_message(const hisq_dd *dd);
+/* Vh_slab, and the records of one halo buffer (3 F) */
+long hisq_dd_half_volume(const hisq_dd *dd);
+long hisq_dd_halo_sites(const hisq_dd *dd);
+/* send_lo = the three lowest time slices of `in` (for the slab below), send_hi = the three
+ * highest (for the slab above): device buffers of 3 F records, stream-ordered.  With t
+ * slowest in the even-odd order each is one contiguous block, copied as such. */
+int hisq_dd_pack(hisq_dd *dd, const double *in, double *send_lo, double *send_hi, void *stream);
+/* out = D_{p,1-p} in on the slab's sites of parity p = out_parity, FP64, with the time
+ * neighbours beyond the slab read from halo_lo / halo_hi.  Device buffers; out must not
+ * overlap any input (HISQ_EINVAL). */
+int hisq_dd_dslash(hisq_dd *dd, int out_parity, const double *in, const double *halo_lo, const double *halo_hi,
+                   double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -114,6 +114,13 @@ _SIGS = {
     "hisq_net_save": (_I, [_P, ctypes.c_char_p]),
     "hisq_net_load": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_P)]),
     "hisq_fcg": (_I, [_P, _D, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats)]),
+    "hisq_dd_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_I), _I, _I, _P, _P, ctypes.POINTER(Opts)]),
+    "hisq_dd_destroy": (None, [_P]),
+    "hisq_dd_last_error_message": (ctypes.c_char_p, [_P]),
+    "hisq_dd_half_volume": (_L, [_P]),
+    "hisq_dd_halo_sites": (_L, [_P]),
+    "hisq_dd_pack": (_I, [_P, _P, _P, _P, _P]),
+    "hisq_dd_dslash": (_I, [_P, _I, _P, _P, _P, _P, _P]),
 }
 
 
@@ -471,6 +478,69 @@ class Field:
     def close(self):
         if getattr(self, "h", None):
             lib().hisq_field_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Domain:
+    """One time slab [t0, t0 + lt) of a domain-decomposed lattice (hisq_dd_*): its Dslash
+    takes the opposite-parity field on the slab plus the two received halos (three time
+    slices each).  Links: the GLOBAL unphased canonical fields (host or device)."""
+
+    def __init__(self, global_dims, t0, lt, fat, lng, device=0):
+        L = lib()
+        o = Opts()
+        L.hisq_opts_default(ctypes.byref(o))
+        o.links_on_device = int(fat.is_cuda)
+        o.device = device
+        d = (ctypes.c_int * 4)(*global_dims)
+        h = ctypes.c_void_p()
+        rc = L.hisq_dd_create(ctypes.byref(h), d, int(t0), int(lt), _ptr(fat), _ptr(lng), ctypes.byref(o))
+        if rc != OK:
+            raise HisqError(rc, L.hisq_strerror(rc).decode())
+        self.h, self.t0, self.lt, self.device = h, int(t0), int(lt), int(device)
+        self.global_dims = tuple(global_dims)
+        self.Vh = L.hisq_dd_half_volume(h)
+        self.halo = L.hisq_dd_halo_sites(h)
+
+    def check(self, rc):
+        if rc != OK:
+            raise HisqError(rc, lib().hisq_dd_last_error_message(self.h).decode())
+        return rc
+
+    def _vec(self, t, n, name):
+        import torch
+        if t.dtype != torch.complex128 or not t.is_cuda or t.device.index != self.device or t.numel() != 3 * n:
+            raise ValueError(f"{name}: complex128 [{n}][3] on cuda:{self.device} expected")
+
+    def halo_buffers(self):
+        """(send_lo, send_hi, recv_lo, recv_hi) device buffers of [3 F][3] complex128."""
+        import torch
+        return tuple(torch.empty(self.halo, 3, dtype=torch.complex128, device=f"cuda:{self.device}") for _ in range(4))
+
+    def pack(self, inp, send_lo, send_hi, stream=None):
+        """The three lowest and three highest time slices of `inp` (one parity)."""
+        self._vec(inp, self.Vh, "in")
+        self._vec(send_lo, self.halo, "send_lo")
+        self._vec(send_hi, self.halo, "send_hi")
+        return self.check(lib().hisq_dd_pack(self.h, _ptr(inp), _ptr(send_lo), _ptr(send_hi), _stream(stream)))
+
+    def dslash(self, out_parity, inp, recv_lo, recv_hi, out, stream=None):
+        self._vec(inp, self.Vh, "in")
+        self._vec(out, self.Vh, "out")
+        self._vec(recv_lo, self.halo, "recv_lo")
+        self._vec(recv_hi, self.halo, "recv_hi")
+        return self.check(lib().hisq_dd_dslash(self.h, int(out_parity), _ptr(inp), _ptr(recv_lo), _ptr(recv_hi),
+                                               _ptr(out), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hisq_dd_destroy(self.h)
             self.h = None
 
     def __del__(self):
