@@ -349,6 +349,20 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         fp64_ms.append(e0.elapsed_time(e1))
     fp64_ms = min(fp64_ms) if fp64_ms else None
+    # plain float-pair CG (FP64-class operator and vectors throughout; the final residual is
+    # recomputed with the FP64 operator): the other FP64-class comparator
+    f64x_ms = []
+    st64x = None
+    for _ in range(args.fp64_reps):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st64x = solve(hisq.F64X, precise=hisq.F64X)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        f64x_ms.append(e0.elapsed_time(e1))
+    f64x_ms = min(f64x_ms) if f64x_ms else None
 
     clk = Clocks(local).__enter__()              # sampling starts with the warm-up
     for _ in range(args.warmup):
@@ -437,6 +451,9 @@ def run_ours(args, world, rank, local):
         from paper_2306_01098_gb300 import dslash_bench
         table = dslash_bench.measure((64, 64, 64, 16), ("f64", "f64x", "f32", "f16"), (1,), 18, hbm_gbs=hbm)
     cb = oracle_sample(args.cpu_seconds, st64.iterations) if not args.no_cpu_baseline else None
+    # the other measured roofs of this GPU (FMA throughput, L2 and HBM read bandwidth, launch
+    # and grid-barrier times), outside the timed region
+    roofs = hisq.measure_peaks(local) if world == 1 else None
     configs = None
     if world == 1 and not args.no_configs:
         del ctx
@@ -458,6 +475,9 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}"},
         "iterations": st.iterations, "reliable_updates": st.reliable_updates, "true_residual": st.true_residual,
         "error_vs_fp64": err_vs_fp64, "fp64_cg_ms": fp64_ms, "fp64_iterations": st64.iterations,
+        "fp64_cg_ms_statistic": f"min of {args.fp64_reps} solves (value: mean of the timed steps)",
+        "f64x_cg_ms": f64x_ms, "f64x_iterations": st64x.iterations if st64x else None,
+        "speedup_vs_f64x_cg": f64x_ms / ms_per_solve if f64x_ms else None,
         "speedup_vs_fp64_cg": fp64_ms / ms_per_solve if fp64_ms else None, "timed_total_ms": total_ms,
         "solve_algorithmic_bytes": solve_bytes,
         "time_to_solution_roof_frac": solve_bytes / (ms_per_solve * 1e-3) / 1e9 / hbm,
@@ -465,7 +485,10 @@ def run_ours(args, world, rank, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic_for(kname), "kernel": kname, "peak_source": src,
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": d_ms * 1e3,
-                     "launches_timed": launches},
+                     "launches_timed": launches,
+                     "l2_peak": roofs["l2_read_gbs"] if roofs else None,
+                     "frac_of_l2": achieved / roofs["l2_read_gbs"] if roofs else None},
+        "measured_roofs": roofs,
         "cpu_baseline": cb,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(b.numel() * 16),
                 "d2h_bytes_per_step": int(b.numel() * 16)},

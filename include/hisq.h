@@ -451,6 +451,25 @@ int hisq_dd_pack(hisq_dd *dd, const double *in, double *send_lo, double *send_hi
 int hisq_dd_dslash(hisq_dd *dd, int out_parity, const double *in, const double *halo_lo, const double *halo_hi,
                    double *out, void *stream);
 
+/* ------------------------------------------------------------------ measured roofs */
+/* Not part of the paper's method: the ceilings of this GPU that the kernels' timings are
+ * compared with, measured on `device` with CUDA events (about 1 s, 2 GB of scratch memory
+ * allocated and freed by the call): fused multiply-add throughput in FP32 and FP64 (8
+ * independent chains per thread, 2048 threads per SM, 2 flops per FMA), read bandwidth of
+ * 16-byte loads through L2 over 64 MB (L2-resident, the time of an empty launch of the same
+ * shape subtracted) and over 2 GB (HBM), the time of one back-to-back launch of an empty
+ * kernel, and one grid-wide barrier of the persistent CG kernel (one 512-thread block per
+ * SM; -1 if a bounded wait ran out). */
+typedef struct {
+    double fp32_tflops;
+    double fp64_tflops;
+    double l2_read_gbs;
+    double hbm_read_gbs;
+    double launch_us;
+    double grid_barrier_us;
+} hisq_peaks;
+int hisq_measure_peaks(int device, hisq_peaks *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -2,6 +2,7 @@
 
   python -m paper_2306_01098_gb300.dslash_bench --dims 64,64,64,16 --prec f64x,f32 --nrhs 1,4 [--comp 12]
   python -m paper_2306_01098_gb300.dslash_bench --prec f32 --nrhs 16 --sweep    # every launch shape
+  python -m paper_2306_01098_gb300.dslash_bench --peaks          # measured ALU, L2, HBM roofs
 
 The timed repetitions run inside an NVTX range named "timed", so that a profiler can be told
 to capture only launches with the autotuned (or pinned) shape.
@@ -114,7 +115,13 @@ def main():
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--shape", default=None, help="n_inner,threads_per_site,site_order instead of the autotuner")
     ap.add_argument("--sweep", action="store_true", help="time every launch shape")
+    ap.add_argument("--peaks", action="store_true",
+                    help="print the measured FMA, L2/HBM, launch and grid-barrier roofs (hisq_measure_peaks)")
     a = ap.parse_args()
+    if a.peaks:
+        from paper_2306_01098_gb300 import hisq
+        print(json.dumps(hisq.measure_peaks()))
+        return
     shape = tuple(int(v) for v in a.shape.split(",")) if a.shape else None
     rows = measure(tuple(int(v) for v in a.dims.split(",")), tuple(a.prec.split(",")),
                    tuple(int(v) for v in a.nrhs.split(",")), a.comp, a.reps, shape=shape, sweep=a.sweep)

@@ -65,6 +65,15 @@ class NetOpts(ctypes.Structure):
                 ("mass", ctypes.c_double), ("tensor_cores", ctypes.c_int), ("selftest_wait", ctypes.c_int)]
 
 
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp32_tflops", ctypes.c_double), ("fp64_tflops", ctypes.c_double),
+                ("l2_read_gbs", ctypes.c_double), ("hbm_read_gbs", ctypes.c_double),
+                ("launch_us", ctypes.c_double), ("grid_barrier_us", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
 
 _SIGS = {
@@ -121,7 +130,18 @@ _SIGS = {
     "hisq_dd_halo_sites": (_L, [_P]),
     "hisq_dd_pack": (_I, [_P, _P, _P, _P, _P]),
     "hisq_dd_dslash": (_I, [_P, _I, _P, _P, _P, _P, _P]),
+    "hisq_measure_peaks": (_I, [_I, ctypes.POINTER(Peaks)]),
 }
+
+
+def measure_peaks(device=0):
+    """Measured FMA throughput, L2/HBM read bandwidth, launch and grid-barrier times
+    (hisq_measure_peaks) as a dict."""
+    p = Peaks()
+    rc = lib().hisq_measure_peaks(int(device), ctypes.byref(p))
+    if rc != OK:
+        raise HisqError(rc, lib().hisq_strerror(rc).decode())
+    return p.as_dict()
 
 
 def exported_symbols():

@@ -12,7 +12,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 STRUCTS = {"hisq_opts": "Opts", "hisq_solve_opts": "SolveOpts", "hisq_stats": "Stats",
-           "hisq_net_opts": "NetOpts"}
+           "hisq_net_opts": "NetOpts", "hisq_peaks": "Peaks"}
 
 
 def _c_layout(tmp_path, hisq):
