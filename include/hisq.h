@@ -134,7 +134,11 @@ size_t hisq_field_bytes(const hisq_field *f);
  * overlap.  `prec` selects the link storage and arithmetic of the applied operator; for
  * prec != HISQ_F64 the vectors are converted on the way in (F64X: float pairs; F32, F16,
  * BF16: FP32) and back to double on the way out.  The 16-bit spinor format is applied
- * through hisq_dslash_field.  Returns HISQ_ENOTBUILT if the context lacks that precision. */
+ * through hisq_dslash_field.  Returns HISQ_ENOTBUILT if the context lacks that precision.
+ * F64X keeps each real as a pair of floats (hi + lo, no per-site scale): its FP64-class
+ * accuracy (about 5e-14 relative per site) holds for vector components of magnitude between
+ * about 1e-30 and 1e37; below, the low word becomes subnormal and accuracy degrades toward
+ * FP32; above, float overflow.  FP64 has the full double range. */
 int hisq_dslash(hisq_ctx *ctx, int out_parity, const double *in, double *out, int nrhs, int prec,
                 void *stream);
 
@@ -172,9 +176,17 @@ int hisq_mdagm_noalloc(hisq_ctx *ctx, double m, const double *in, double *out, i
  * order (t slowest), 1 z and t interchanged (allowed when Nt < Nz and one z-t plane,
  * Nx/2 * Ny sites, is a multiple of 32), -1 the size-based default.  Vector precision equals
  * the link precision, or is HISQ_F32 with 16-bit links.  Results do not depend on the shape
- * beyond the rounding order of the reductions.  Returns HISQ_EINVAL for any other value. */
+ * beyond the rounding order of the reductions.  Returns HISQ_EINVAL for any other value.
+ * The autotuner also searches 64, 128 and 256 threads per block (hisq_tune_set_block). */
 int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int n_inner, int threads_per_site,
                   int site_order);
+/* Threads per block (64, 128 or 256; sites per block = threads / threads_per_site) of the shape
+ * already stored for the key (by the autotuner or hisq_tune_set, which stores 128); batches of
+ * lattices run 128.  HISQ_EINVAL if no shape is stored or the value is not allowed. */
+int hisq_tune_set_block(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int threads_per_block);
+/* The stored shape for the key: shape = {n_inner, threads_per_site, site_order,
+ * threads_per_block}; HISQ_EINVAL if none is stored yet. */
+int hisq_tune_get(const hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int shape[4]);
 
 /* ------------------------------------------------------------------ solvers */
 typedef struct {
@@ -454,7 +466,7 @@ int hisq_dd_dslash(hisq_dd *dd, int out_parity, const double *in, const double *
 /* ------------------------------------------------------------------ measured roofs */
 /* Not part of the paper's method: the ceilings of this GPU that the kernels' timings are
  * compared with, measured on `device` with CUDA events (about 1 s, 2 GB of scratch memory
- * allocated and freed by the call): fused multiply-add throughput in FP32 and FP64 (8
+ * allocated and freed by the call): fused multiply-add throughput in FP32 and FP64 (8 and 16
  * independent chains per thread, 2048 threads per SM, 2 flops per FMA), read bandwidth of
  * 16-byte loads through L2 over 64 MB (L2-resident, the time of an empty launch of the same
  * shape subtracted) and over 2 GB (HBM), the time of one back-to-back launch of an empty

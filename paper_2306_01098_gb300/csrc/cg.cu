@@ -209,7 +209,7 @@ int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out)
     W.rb64 = (size_t)ctx->g.Vh * 48;
     W.rbP = (size_t)ctx->g.VhPad * 48;
     W.nblk_vec = (int)std::min<long>((W.Vh + kVecBlock - 1) / kVecBlock, 4L * ctx->sm_count);
-    W.nblk_dslash = (int)((4ull * W.Vh + kDslashBlock - 1) / kDslashBlock); // blocks at 4 threads per site (upper bound)
+    W.nblk_dslash = (int)((4ull * W.Vh + 63) / 64); // blocks at 4 threads per site and 64 threads per block (upper bound)
     int rc = HISQ_OK;
     auto A = [&](char **p, size_t b) { if (rc == HISQ_OK) rc = W.alloc(ctx, p, b); };
     A(&W.r, W.rbS * nrhs);

@@ -23,6 +23,7 @@ cudaError_t dslash_launch(int pl, int pv, int epi, const DslashArgs &a, int nrea
     const int nr = sh.nr, ds = sh.ds;
     DslashArgs b = a;
     b.zt = sh.order;
+    b.bs = sh.bs;
     if (pl == pv) {
         switch (pl) {
         case HISQ_F64: return dslash_launch_HISQ_F64_HISQ_F64(epi, b, nreal, nr, ds, st);
@@ -55,6 +56,7 @@ DslashArgs make_dslash_args(hisq_ctx *ctx, int prec, int out_parity, const void 
     a.nrhs = nrhs;
     a.stream_links = L.slot_bytes * kSlots > ctx->l2_persist_max;
     a.sm_count = ctx->sm_count;
+    a.bs = kDslashBlock;
     if (ctx->batch) {
         a.batch = ctx->batch;
         a.batch_n = ctx->batch_host->n;
@@ -83,11 +85,11 @@ static DslashShape default_shape(hisq_ctx *ctx, int pv, int nrhs)
     return s;
 }
 
-// Autotuner: every (N_inner, threads-per-site, site order) shape that divides the work is
-// timed on the caller's buffers (best of two rounds of 3 launches after one warm-up, CUDA
-// events on the caller's stream) the first time a key is seen; a shape replaces the
-// size-based default only when it is at least 3% faster.  The choice is kept for the
-// context's lifetime.
+// Autotuner: every (N_inner, threads-per-site, site order, threads per block) shape that
+// divides the work is timed on the caller's buffers (best of two rounds of 3 launches after
+// one warm-up, CUDA events on the caller's stream) the first time a key is seen; a shape
+// replaces the size-based default only when it is at least 3% faster.  The choice is kept
+// for the context's lifetime.  (A batch of lattices always runs 128-thread blocks.)
 DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in, void *out, size_t rhs_bytes,
                          cudaStream_t st)
 {
@@ -131,18 +133,20 @@ DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in
     };
     const DslashShape def = best;
     float best_ms = time_shape(def);
+    const int bs_max = ctx->batch ? kDslashBlock : kDslashMaxBlock;
     for (int order = 0; order <= (ctx->g.zt_ok ? 1 : 0); order++)
         for (int nr = 1; nr <= cap; nr <<= 1) {
             if (nrhs % nr) continue;
-            for (int ds = 1; ds <= 4; ds <<= 1) {
-                DslashShape sh{nr, ds, order};
-                if (sh.nr == def.nr && sh.ds == def.ds && sh.order == def.order) continue;
-                const float ms = time_shape(sh);
-                if (ms < 0.97f * best_ms) {
-                    best_ms = ms;
-                    best = sh;
+            for (int ds = 1; ds <= 4; ds <<= 1)
+                for (int bs = ctx->batch ? kDslashBlock : 64; bs <= bs_max; bs <<= 1) {
+                    DslashShape sh{nr, ds, order, bs};
+                    if (sh.nr == def.nr && sh.ds == def.ds && sh.order == def.order && sh.bs == def.bs) continue;
+                    const float ms = time_shape(sh);
+                    if (ms < 0.97f * best_ms) {
+                        best_ms = ms;
+                        best = sh;
+                    }
                 }
-            }
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -184,7 +188,31 @@ extern "C" int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, in
         site_order < -1 || site_order > 1 || (site_order == 1 && !ctx->g.zt_ok))
         return set_error(ctx, HISQ_EINVAL, "hisq_tune_set: bad shape");
     const int order = site_order >= 0 ? site_order : default_order(ctx, prec_vectors, nrhs);
-    ctx->tune[tune_key(prec_links, prec_vectors, nrhs)] = DslashShape{n_inner, threads_per_site, order};
+    ctx->tune[tune_key(prec_links, prec_vectors, nrhs)] = DslashShape{n_inner, threads_per_site, order, kDslashBlock};
+    return HISQ_OK;
+}
+
+extern "C" int hisq_tune_set_block(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int threads_per_block)
+{
+    if (!ctx) return HISQ_EINVAL;
+    auto it = ctx->tune.find(tune_key(prec_links, prec_vectors, nrhs));
+    if (it == ctx->tune.end()) return set_error(ctx, HISQ_EINVAL, "hisq_tune_set_block: no shape for this key");
+    if ((threads_per_block != 64 && threads_per_block != 128 && threads_per_block != 256) ||
+        (ctx->batch && threads_per_block != kDslashBlock))
+        return set_error(ctx, HISQ_EINVAL, "hisq_tune_set_block: threads per block must be 64, 128 or 256");
+    it->second.bs = threads_per_block;
+    return HISQ_OK;
+}
+
+extern "C" int hisq_tune_get(const hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int shape[4])
+{
+    if (!ctx || !shape) return HISQ_EINVAL;
+    auto it = ctx->tune.find(tune_key(prec_links, prec_vectors, nrhs));
+    if (it == ctx->tune.end()) return HISQ_EINVAL;
+    shape[0] = it->second.nr;
+    shape[1] = it->second.ds;
+    shape[2] = it->second.order;
+    shape[3] = it->second.bs;
     return HISQ_OK;
 }
 

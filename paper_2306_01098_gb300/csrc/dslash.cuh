@@ -6,7 +6,8 @@
 
 namespace hisq {
 
-constexpr int kDslashBlock = 128;
+constexpr int kDslashBlock = 128;    // threads per block of batches and the default shape
+constexpr int kDslashMaxBlock = 256; // largest block size of the autotuner's search
 
 struct DslashArgs {
     Geom g;
@@ -29,6 +30,7 @@ struct DslashArgs {
     int zt;                // launch order with z and t interchanged (Geom::zt_ok required)
     int stream_links;      // link store larger than L2 can keep: load links evict-first
     int sm_count;          // SMs of the device (grid size)
+    int bs;                // threads per block (64, 128 or 256; batches: kDslashBlock)
     uint32_t items;        // work items of the launch (set by the launcher)
     // batch of lattices (NULL for one lattice): device table, lattices, and from the host
     // copy of the table the tiles of all lattices / of the largest, per threads per site

@@ -93,7 +93,7 @@ __device__ __forceinline__ void vec_load(const char *base, uint32_t s, typename 
     else T::load(base, s, v);
 }
 
-// One work item: the sites of one tile (kDslashBlock threads, DS per site; this thread is
+// One work item: the sites of one tile (a.bs threads, DS per site; this thread is
 // number tid of the tile) for the NR right-hand sides whose vectors start at in/out/pv/rv
 // (consecutive right-hand sides a.rhs_bytes apart); geometry g, link store `links`.
 // Epilogue dot products are added to dots (value j of right-hand side r at
@@ -115,7 +115,7 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
     constexpr bool TWO = (PL == HISQ_F16 || PL == HISQ_BF16 || NREAL == 12);
     constexpr bool SPLIT = T::kSplitDirections;
     constexpr int NMU = 4 / DS;
-    const uint32_t gt = tile * kDslashBlock + tid;
+    const uint32_t gt = tile * (uint32_t)a.bs + tid;
     const uint32_t u = gt / DS; // site number in launch order
     const int part = (int)(gt % DS);
     const bool live = u < g.Vh;
@@ -250,7 +250,7 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
 
 // BATCH: the lattices of a batch in one launch (NR = 1; right-hand side k is lattice k).
 template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH>
-__global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
+__global__ void __launch_bounds__(kDslashMaxBlock) k_dslash(const DslashArgs a)
 {
     using T = Prec<PV>;
     using TL = Prec<PL>;
@@ -332,16 +332,20 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const DslashArgs a)
 template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH>
 static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
 {
-    static int occ = -1; // resident blocks per SM of this instantiation
-    if (occ < 0) {
+    DslashArgs a = a0;
+    const int bs = BATCH ? kDslashBlock : a.bs;
+    if (bs != 64 && bs != 128 && bs != 256) return cudaErrorInvalidValue;
+    a.bs = bs;
+    static int occ[3] = {-1, -1, -1}; // resident blocks per SM of this instantiation, per block size
+    const int bi = bs == 64 ? 0 : bs == 128 ? 1 : 2;
+    if (occ[bi] < 0) {
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_dslash<PL, PV, NREAL, NR, EPI, DS, BATCH>, kDslashBlock,
-                                                          0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_dslash<PL, PV, NREAL, NR, EPI, DS, BATCH>, bs, 0) !=
+                cudaSuccess ||
             o < 1)
             o = 1;
-        occ = o;
+        occ[bi] = o;
     }
-    DslashArgs a = a0;
     if constexpr (BATCH) { // one block per tile of every lattice
         constexpr int d = DS == 1 ? 0 : DS == 2 ? 1 : 2;
         const uint32_t items = a.batch_tiles[d];
@@ -351,16 +355,16 @@ static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
         k_dslash<PL, PV, NREAL, 1, EPI, DS, true><<<items, kDslashBlock, 0, st>>>(a);
         return cudaGetLastError();
     } else {
-        const size_t tiles = ((size_t)a.g.Vh * DS + kDslashBlock - 1) / kDslashBlock;
+        const size_t tiles = ((size_t)a.g.Vh * DS + bs - 1) / bs;
         const size_t ng = (size_t)(a.nrhs / NR);
         const size_t items = tiles * ng;
-        const size_t resident = std::max<size_t>(ng, (size_t)std::max(1, a.sm_count) * occ / ng * ng);
+        const size_t resident = std::max<size_t>(ng, (size_t)std::max(1, a.sm_count) * occ[bi] / ng * ng);
         const size_t blocks = a.red.partials ? std::min(items, resident) : items;
         if (items > 0xffffffffull) return cudaErrorInvalidValue;
         a.items = (uint32_t)items;
         a.red.nblocks = (int)(blocks / ng); // partials per right-hand side
         a.red.ntotal = (int)blocks;
-        k_dslash<PL, PV, NREAL, NR, EPI, DS, false><<<(unsigned)blocks, kDslashBlock, 0, st>>>(a);
+        k_dslash<PL, PV, NREAL, NR, EPI, DS, false><<<(unsigned)blocks, bs, 0, st>>>(a);
         return cudaGetLastError();
     }
 }

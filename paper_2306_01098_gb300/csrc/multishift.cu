@@ -240,7 +240,7 @@ static int get_ms_work(hisq_ctx *ctx, int nshift, int ps, MsWork **out)
     W.rbX = (size_t)ctx->g.VhPad * spinor_bytes(W.px);
     W.rb64 = (size_t)ctx->g.Vh * 48;
     W.nblk_vec = (int)std::min<long>((W.Vh + kVecBlock - 1) / kVecBlock, 4L * ctx->sm_count);
-    W.nblk_dslash = (int)((4ull * W.Vh + kDslashBlock - 1) / kDslashBlock); // blocks at 4 threads per site (upper bound)
+    W.nblk_dslash = (int)((4ull * W.Vh + 63) / 64); // blocks at 4 threads per site and 64 threads per block (upper bound)
     int rc = HISQ_OK;
     auto A = [&](char **p, size_t b) { if (rc == HISQ_OK) rc = ms_alloc(ctx, W, p, b); };
     A(&W.r, W.rbS);

@@ -33,6 +33,7 @@ int apply_mdagm(hisq_ctx *ctx, int prec, double m, const void *in, void *tmp, vo
         sh.nr = it != ctx->tune.end() ? it->second.nr : pick_inner(pv, nrhs);
         sh.ds = it != ctx->tune.end() ? it->second.ds : (ctx->g.Vh < (1u << 20) ? 2 : 1);
         sh.order = it != ctx->tune.end() ? it->second.order : 0;
+        sh.bs = it != ctx->tune.end() ? it->second.bs : kDslashBlock;
     }
     DslashArgs a = make_dslash_args(ctx, prec, 1, in, tmp, nrhs, rhs_bytes);
     cudaError_t e = dslash_launch(prec, pv, 0, a, L.nreal, sh, st);

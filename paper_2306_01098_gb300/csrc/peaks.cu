@@ -9,22 +9,20 @@
 
 namespace hisq {
 
-constexpr int kPeakChains = 8;
-
-// each thread: kPeakChains independent FMA chains of n steps (2 flops per FMA)
-template <class R>
+// each thread: C independent FMA chains of n steps (2 flops per FMA)
+template <class R, int C>
 __global__ void __launch_bounds__(256) k_peak_fma(int n, R a, R b, R *out)
 {
-    R v[kPeakChains];
+    R v[C];
 #pragma unroll
-    for (int c = 0; c < kPeakChains; c++) v[c] = (R)(threadIdx.x + c);
+    for (int c = 0; c < C; c++) v[c] = (R)(threadIdx.x + c);
     for (int i = 0; i < n; i++) {
 #pragma unroll
-        for (int c = 0; c < kPeakChains; c++) v[c] = v[c] * a + b;
+        for (int c = 0; c < C; c++) v[c] = v[c] * a + b;
     }
     R s = 0;
 #pragma unroll
-    for (int c = 0; c < kPeakChains; c++) s += v[c];
+    for (int c = 0; c < C; c++) s += v[c];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
@@ -94,11 +92,11 @@ extern "C" int hisq_measure_peaks(int device, hisq_peaks *out)
     if (e == cudaSuccess) {
         // long enough (tens of ms) for the clocks and pipes to settle
         const int n = 65536;
-        double ms = time_ms([&] { k_peak_fma<float><<<blocks, threads>>>(n, 0.999f, 0.5f, (float *)res); }, 5);
-        out->fp32_tflops = 2.0 * kPeakChains * n * (double)blocks * threads / (ms * 1e-3) / 1e12;
-        const int nd = 4096;
-        ms = time_ms([&] { k_peak_fma<double><<<blocks, threads>>>(nd, 0.999, 0.5, (double *)res); }, 5);
-        out->fp64_tflops = 2.0 * kPeakChains * nd * (double)blocks * threads / (ms * 1e-3) / 1e12;
+        double ms = time_ms([&] { k_peak_fma<float, 8><<<blocks, threads>>>(n, 0.999f, 0.5f, (float *)res); }, 5);
+        out->fp32_tflops = 2.0 * 8 * n * (double)blocks * threads / (ms * 1e-3) / 1e12;
+        const int nd = 2048;
+        ms = time_ms([&] { k_peak_fma<double, 16><<<blocks, threads>>>(nd, 0.999, 0.5, (double *)res); }, 5);
+        out->fp64_tflops = 2.0 * 16 * nd * (double)blocks * threads / (ms * 1e-3) / 1e12;
         const int rb = 4 * sms;
         ms = time_ms([&] { k_peak_read<<<rb, threads>>>((const uint4 *)buf, l2_bytes / 16, (unsigned *)res); }, 20);
         // the empty launch of the same shape is subtracted: a single pass over 64 MB is short

@@ -43,14 +43,15 @@ def hbm_peak():
 
 
 def shapes(prec, nrhs, zt_ok=True):
-    """Every (n_inner, threads per site, site order) launch shape the autotuner considers."""
+    """Every (n_inner, threads per site, site order, threads per block) launch shape the
+    autotuner considers."""
     cap = 4 if prec in ("f64", "f64x") else 8
     out = []
     for order in ((0, 1) if zt_ok else (0,)):
         nr = 1
         while nr <= cap:
             if nrhs % nr == 0:
-                out.extend((nr, ds, order) for ds in (1, 2, 4))
+                out.extend((nr, ds, order, bs) for ds in (1, 2, 4) for bs in (64, 128, 256))
             nr *= 2
     return out
 
@@ -77,7 +78,9 @@ def measure(dims=(64, 64, 64, 16), precs=("f64", "f64x", "f32", "f16"), nrhs_lis
             pinned = shapes(hisq.PREC_NAMES[p], nrhs, zt_ok) if sweep else [shape]
             for sh in pinned:
                 if sh is not None:
-                    ctx.tune_set(p, p, nrhs, *sh)
+                    ctx.tune_set(p, p, nrhs, *sh[:3])
+                    if len(sh) > 3:
+                        ctx.tune_set_block(p, p, nrhs, sh[3])
                 for _ in range(3):
                     ctx.dslash_field(0, fi, fo)
                 torch.cuda.synchronize()
@@ -97,8 +100,10 @@ def measure(dims=(64, 64, 64, 16), precs=("f64", "f64x", "f32", "f16"), nrhs_lis
                 row = {"prec": hisq.PREC_NAMES[p], "nreal": comp, "nrhs": nrhs, "us": ms * 1e3,
                        "gbs": b / ms / 1e6, "frac_hbm": b / ms / 1e6 / hbm_gbs,
                        "tflops": 1146 * ctx.Vh * nrhs / ms / 1e9, "bytes": b}
-                if sh is not None:
-                    row["shape"] = {"n_inner": sh[0], "threads_per_site": sh[1], "site_order": sh[2]}
+                used = ctx.tune_get(p, p, nrhs)
+                if used is not None:
+                    row["shape"] = {"n_inner": used[0], "threads_per_site": used[1], "site_order": used[2],
+                                    "threads_per_block": used[3], "autotuned": sh is None}
                 out.append(row)
             fi.close()
             fo.close()
@@ -113,7 +118,8 @@ def main():
     ap.add_argument("--nrhs", default="1")
     ap.add_argument("--comp", type=int, default=18)
     ap.add_argument("--reps", type=int, default=10)
-    ap.add_argument("--shape", default=None, help="n_inner,threads_per_site,site_order instead of the autotuner")
+    ap.add_argument("--shape", default=None,
+                    help="n_inner,threads_per_site,site_order[,threads_per_block] instead of the autotuner")
     ap.add_argument("--sweep", action="store_true", help="time every launch shape")
     ap.add_argument("--peaks", action="store_true",
                     help="print the measured FMA, L2/HBM, launch and grid-barrier roofs (hisq_measure_peaks)")

@@ -120,7 +120,8 @@ def test_dslash_multi_rhs(nrhs, prec):
 
 @pytest.mark.parametrize("prec", [hisq.F64, hisq.F64X, hisq.F32, hisq.F16, hisq.BF16])
 def test_dslash_every_launch_shape(prec):
-    # every (right-hand sides per thread, threads per site) shape gives the same operator
+    # every (right-hand sides per thread, threads per site, threads per block) shape gives the
+    # same operator
     dims, nrhs = (6, 4, 4, 8), 8
     ctx, fat, lng = setup(dims)
     x = fields.gaussian_source(dims, 170, nrhs)
@@ -131,15 +132,19 @@ def test_dslash_every_launch_shape(prec):
         if nr == 8 and prec in (hisq.F64, hisq.F64X):
             continue
         for ds in (1, 2, 4):
-            ctx.tune_set(prec, pv, nrhs, nr, ds)
-            out = torch.full_like(x, float("nan")).cuda()
-            ctx.dslash(0, x.cuda(), out, prec=prec)
-            got = out.cpu().numpy()
-            for r in range(nrhs):
-                if tol is None:
-                    assert site_rel(got[r], want[r]) <= 1e-13, (nr, ds, r)
-                else:
-                    assert field_rel(got[r], want[r]) <= tol, (nr, ds, r)
+            for bs in (64, 128, 256):
+                ctx.tune_set(prec, pv, nrhs, nr, ds)
+                ctx.tune_set_block(prec, pv, nrhs, bs)
+                got_shape = ctx.tune_get(prec, pv, nrhs)
+                assert got_shape[0] == nr and got_shape[1] == ds and got_shape[3] == bs
+                out = torch.full_like(x, float("nan")).cuda()
+                ctx.dslash(0, x.cuda(), out, prec=prec)
+                got = out.cpu().numpy()
+                for r in range(nrhs):
+                    if tol is None:
+                        assert site_rel(got[r], want[r]) <= 1e-13, (nr, ds, bs, r)
+                    else:
+                        assert field_rel(got[r], want[r]) <= tol, (nr, ds, bs, r)
     _cache.clear()
 
 
@@ -398,3 +403,18 @@ def test_12_real_every_site_large_lattice(prec, u):
                 worst = max(worst, check_sites(got[r], want[r], S[r], factor, (nrhs, nr, ds, order, r)))
         del want, S, x
     print(f"{hisq.PREC_NAMES[prec]} 12-real 64^3x16: worst site at {worst:.3f} of the quantisation bound")
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e30])
+def test_float_pair_range(scale):
+    # HISQ_F64X keeps every real as a float pair hi + lo without a per-site scale: inputs whose
+    # components lie between about 1e-30 (the low word still a normal float) and 1e37 (the
+    # products below float overflow) keep the 1e-13 per-site bound; the header states the range
+    dims = (8, 6, 4, 6)
+    ctx, fat, lng = setup(dims, precs=(hisq.F64, hisq.F64X))
+    for p in (0, 1):
+        x = (fields.gaussian_source(dims, 190 + p)[0] * scale).contiguous()
+        out = torch.full_like(x, float("nan")).cuda()
+        ctx.dslash(p, x.cuda(), out, prec=hisq.F64X)
+        want = oracle.dslash(dims, fat, lng, x, p)
+        assert site_rel(out.cpu().numpy(), want) <= 1e-13, (scale, p)
