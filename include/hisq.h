@@ -177,16 +177,23 @@ int hisq_mdagm_noalloc(hisq_ctx *ctx, double m, const double *in, double *out, i
  * Nx/2 * Ny sites, is a multiple of 32), -1 the size-based default.  Vector precision equals
  * the link precision, or is HISQ_F32 with 16-bit links.  Results do not depend on the shape
  * beyond the rounding order of the reductions.  Returns HISQ_EINVAL for any other value.
- * The autotuner also searches 64, 128 and 256 threads per block (hisq_tune_set_block). */
+ * The autotuner also searches 64, 128 and 256 threads per block (hisq_tune_set_block) and
+ * groups of right-hand sides sharing a site (hisq_tune_set_groups). */
 int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int n_inner, int threads_per_site,
                   int site_order);
 /* Threads per block (64, 128 or 256; sites per block = threads / threads_per_site) of the shape
  * already stored for the key (by the autotuner or hisq_tune_set, which stores 128); batches of
  * lattices run 128.  HISQ_EINVAL if no shape is stored or the value is not allowed. */
 int hisq_tune_set_block(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int threads_per_block);
+/* Groups of right-hand sides per site (1, 2 or 4) of the stored shape: with g > 1, g
+ * consecutive threads share one site (threads_per_site must be 1), thread k of them taking
+ * right-hand sides k n_inner .. k n_inner + n_inner - 1 of its group of g n_inner, so each link
+ * is loaded once for all of them (n_inner <= 4, g n_inner dividing nrhs).  Results do not
+ * depend on it beyond the rounding order of the reductions.  HISQ_EINVAL otherwise. */
+int hisq_tune_set_groups(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int rhs_groups);
 /* The stored shape for the key: shape = {n_inner, threads_per_site, site_order,
- * threads_per_block}; HISQ_EINVAL if none is stored yet. */
-int hisq_tune_get(const hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int shape[4]);
+ * threads_per_block, rhs_groups}; HISQ_EINVAL if none is stored yet. */
+int hisq_tune_get(const hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int shape[5]);
 
 /* ------------------------------------------------------------------ solvers */
 typedef struct {

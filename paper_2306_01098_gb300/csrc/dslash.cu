@@ -26,15 +26,15 @@ cudaError_t dslash_launch(int pl, int pv, int epi, const DslashArgs &a, int nrea
     b.bs = sh.bs;
     if (pl == pv) {
         switch (pl) {
-        case HISQ_F64: return dslash_launch_HISQ_F64_HISQ_F64(epi, b, nreal, nr, ds, st);
-        case HISQ_F64X: return dslash_launch_HISQ_F64X_HISQ_F64X(epi, b, nreal, nr, ds, st);
-        case HISQ_F32: return dslash_launch_HISQ_F32_HISQ_F32(epi, b, nreal, nr, ds, st);
-        case HISQ_F16: return dslash_launch_HISQ_F16_HISQ_F16(epi, b, nreal, nr, ds, st);
-        case HISQ_BF16: return dslash_launch_HISQ_BF16_HISQ_BF16(epi, b, nreal, nr, ds, st);
+        case HISQ_F64: return dslash_launch_HISQ_F64_HISQ_F64(epi, b, nreal, nr, ds, sh.rg, st);
+        case HISQ_F64X: return dslash_launch_HISQ_F64X_HISQ_F64X(epi, b, nreal, nr, ds, sh.rg, st);
+        case HISQ_F32: return dslash_launch_HISQ_F32_HISQ_F32(epi, b, nreal, nr, ds, sh.rg, st);
+        case HISQ_F16: return dslash_launch_HISQ_F16_HISQ_F16(epi, b, nreal, nr, ds, sh.rg, st);
+        case HISQ_BF16: return dslash_launch_HISQ_BF16_HISQ_BF16(epi, b, nreal, nr, ds, sh.rg, st);
         }
     } else if (pv == HISQ_F32) {
-        if (pl == HISQ_F16) return dslash_launch_HISQ_F16_HISQ_F32(epi, b, nreal, nr, ds, st);
-        if (pl == HISQ_BF16) return dslash_launch_HISQ_BF16_HISQ_F32(epi, b, nreal, nr, ds, st);
+        if (pl == HISQ_F16) return dslash_launch_HISQ_F16_HISQ_F32(epi, b, nreal, nr, ds, sh.rg, st);
+        if (pl == HISQ_BF16) return dslash_launch_HISQ_BF16_HISQ_F32(epi, b, nreal, nr, ds, sh.rg, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -138,13 +138,18 @@ DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in
         for (int nr = 1; nr <= cap; nr <<= 1) {
             if (nrhs % nr) continue;
             for (int ds = 1; ds <= 4; ds <<= 1)
-                for (int bs = ctx->batch ? kDslashBlock : 64; bs <= bs_max; bs <<= 1) {
-                    DslashShape sh{nr, ds, order, bs};
-                    if (sh.nr == def.nr && sh.ds == def.ds && sh.order == def.order && sh.bs == def.bs) continue;
-                    const float ms = time_shape(sh);
-                    if (ms < 0.97f * best_ms) {
-                        best_ms = ms;
-                        best = sh;
+                for (int rg = 1; rg <= (ds == 1 && !ctx->batch && nr <= 4 ? 4 : 1); rg <<= 1) {
+                    if (nrhs % (nr * rg)) continue;
+                    for (int bs = ctx->batch ? kDslashBlock : 64; bs <= bs_max; bs <<= 1) {
+                        DslashShape sh{nr, ds, order, bs, rg};
+                        if (sh.nr == def.nr && sh.ds == def.ds && sh.order == def.order && sh.bs == def.bs &&
+                            sh.rg == def.rg)
+                            continue;
+                        const float ms = time_shape(sh);
+                        if (ms < 0.97f * best_ms) {
+                            best_ms = ms;
+                            best = sh;
+                        }
                     }
                 }
         }
@@ -188,7 +193,7 @@ extern "C" int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, in
         site_order < -1 || site_order > 1 || (site_order == 1 && !ctx->g.zt_ok))
         return set_error(ctx, HISQ_EINVAL, "hisq_tune_set: bad shape");
     const int order = site_order >= 0 ? site_order : default_order(ctx, prec_vectors, nrhs);
-    ctx->tune[tune_key(prec_links, prec_vectors, nrhs)] = DslashShape{n_inner, threads_per_site, order, kDslashBlock};
+    ctx->tune[tune_key(prec_links, prec_vectors, nrhs)] = DslashShape{n_inner, threads_per_site, order, kDslashBlock, 1};
     return HISQ_OK;
 }
 
@@ -204,7 +209,21 @@ extern "C" int hisq_tune_set_block(hisq_ctx *ctx, int prec_links, int prec_vecto
     return HISQ_OK;
 }
 
-extern "C" int hisq_tune_get(const hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int shape[4])
+extern "C" int hisq_tune_set_groups(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int rhs_groups)
+{
+    if (!ctx) return HISQ_EINVAL;
+    auto it = ctx->tune.find(tune_key(prec_links, prec_vectors, nrhs));
+    if (it == ctx->tune.end()) return set_error(ctx, HISQ_EINVAL, "hisq_tune_set_groups: no shape for this key");
+    const DslashShape &sh = it->second;
+    if ((rhs_groups != 1 && rhs_groups != 2 && rhs_groups != 4) ||
+        (rhs_groups > 1 && (sh.ds != 1 || sh.nr > 4 || ctx->batch)) || nrhs % (sh.nr * rhs_groups))
+        return set_error(ctx, HISQ_EINVAL, "hisq_tune_set_groups: groups must be 1, 2 or 4, with one thread per "
+                                           "site, n_inner <= 4 and n_inner * groups dividing nrhs");
+    it->second.rg = rhs_groups;
+    return HISQ_OK;
+}
+
+extern "C" int hisq_tune_get(const hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int shape[5])
 {
     if (!ctx || !shape) return HISQ_EINVAL;
     auto it = ctx->tune.find(tune_key(prec_links, prec_vectors, nrhs));
@@ -213,6 +232,7 @@ extern "C" int hisq_tune_get(const hisq_ctx *ctx, int prec_links, int prec_vecto
     shape[1] = it->second.ds;
     shape[2] = it->second.order;
     shape[3] = it->second.bs;
+    shape[4] = it->second.rg;
     return HISQ_OK;
 }
 

@@ -53,7 +53,8 @@ DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in
 int pick_inner(int prec, int nrhs);
 
 #define HISQ_DSLASH_DECLARE(PL, PV) \
-    cudaError_t dslash_launch_##PL##_##PV(int epi, const DslashArgs &a, int nreal, int nr, int ds, cudaStream_t st);
+    cudaError_t dslash_launch_##PL##_##PV(int epi, const DslashArgs &a, int nreal, int nr, int ds, int rg,      \
+                                          cudaStream_t st);
 HISQ_DSLASH_DECLARE(HISQ_F64, HISQ_F64)
 HISQ_DSLASH_DECLARE(HISQ_F64X, HISQ_F64X)
 HISQ_DSLASH_DECLARE(HISQ_F32, HISQ_F32)

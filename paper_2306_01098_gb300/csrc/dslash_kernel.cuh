@@ -101,13 +101,18 @@ __device__ __forceinline__ void vec_load(const char *base, uint32_t s, typename 
 // site s - ebase (ebase = 0: the whole field; else a block's own range, e.g. in shared memory).
 // PF: issue the loads of all four hops of a direction before their products (more requests
 // in flight per thread, more registers).
-template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool COH = false, bool PF = false>
+// RG > 1 (with DS = 1): RG consecutive threads share a site, thread g of them taking the NR
+// right-hand sides g NR .. g NR + NR - 1 from the given ones; their loads of the site's links
+// are the same addresses in the same instruction (one request), so a link is fetched once
+// for all NR RG right-hand sides with 1/RG of the accumulators per thread.
+template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool COH = false, bool PF = false, int RG = 1>
 __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, const char *links, size_t slot_bytes,
                                             double sc0, double sc1, const char *in, char *outp, const char *pvp,
                                             const char *rvp, const double *m4r, uint32_t tile,
                                             double (&dots)[NR * EpiDots<EPI>::n], uint32_t tid = threadIdx.x,
                                             uint32_t ebase = 0)
 {
+    static_assert(RG == 1 || DS == 1, "right-hand side groups share a site only with one thread per direction set");
     constexpr int ND = EpiDots<EPI>::n;
     using T = Prec<PV>;  // vectors and arithmetic
     using TL = Prec<PL>; // link storage
@@ -116,8 +121,16 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
     constexpr bool SPLIT = T::kSplitDirections;
     constexpr int NMU = 4 / DS;
     const uint32_t gt = tile * (uint32_t)a.bs + tid;
-    const uint32_t u = gt / DS; // site number in launch order
+    const uint32_t u = gt / (DS * RG); // site number in launch order
     const int part = (int)(gt % DS);
+    if constexpr (RG > 1) {
+        const size_t goff = (size_t)(gt % RG) * NR * a.rhs_bytes;
+        in += goff;
+        outp += goff;
+        if (pvp) pvp += goff;
+        if (rvp) rvp += goff;
+        if (m4r) m4r += (gt % RG) * NR;
+    }
     const bool live = u < g.Vh;
     uint32_t s = u;
     if (a.zt) { // u = ((z Nt + t) Ps + i)  ->  s = ((t Nz + z) Ps + i), Ps = sites of one plane
@@ -249,7 +262,8 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
 }
 
 // BATCH: the lattices of a batch in one launch (NR = 1; right-hand side k is lattice k).
-template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH>
+// RG: groups of right-hand sides sharing a site's threads (dslash_item).
+template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH, int RG = 1>
 __global__ void __launch_bounds__(kDslashMaxBlock) k_dslash(const DslashArgs a)
 {
     using T = Prec<PV>;
@@ -306,18 +320,24 @@ __global__ void __launch_bounds__(kDslashMaxBlock) k_dslash(const DslashArgs a)
     } else {
         // gridDim.x is a multiple of the group count, so a block keeps one group of right-hand
         // sides while it strides over the work items (site tile, group)
-        const uint32_t ngroups = (uint32_t)(a.nrhs / NR);
-        const int rhs0 = (int)(blockIdx.x % ngroups) * NR;
+        const uint32_t ngroups = (uint32_t)(a.nrhs / (NR * RG));
+        const int rhs0 = (int)(blockIdx.x % ngroups) * NR * RG;
         const size_t off = (size_t)rhs0 * a.rhs_bytes;
         for (uint32_t item = blockIdx.x; item < a.items; item += gridDim.x)
-            dslash_item<PL, PV, NREAL, NR, EPI, DS>(a, a.g, a.links, a.slot_bytes, a.scale[0], a.scale[1], a.in + off,
-                                                    a.out + off, EPI ? a.pv + off : nullptr,
-                                                    EPI == 2 ? a.rv + off : nullptr,
-                                                    a.shift ? a.shift + rhs0 : nullptr, item / ngroups, dots);
+            dslash_item<PL, PV, NREAL, NR, EPI, DS, false, false, RG>(
+                a, a.g, a.links, a.slot_bytes, a.scale[0], a.scale[1], a.in + off, a.out + off,
+                EPI ? a.pv + off : nullptr, EPI == 2 ? a.rv + off : nullptr, a.shift ? a.shift + rhs0 : nullptr,
+                item / ngroups, dots);
         if constexpr (EPI >= 1) {
             if (a.red.partials) { // uniform over the grid
-                block_sum_multi<NR * ND>(dots);
-                grid_reduce<NR * ND>(a.red, dots, NR * ND, ND * rhs0, ND * a.nrhs, (int)(blockIdx.x / ngroups));
+                if constexpr (RG == 1) {
+                    block_sum_multi<NR * ND>(dots);
+                    grid_reduce<NR * ND>(a.red, dots, NR * ND, ND * rhs0, ND * a.nrhs, (int)(blockIdx.x / ngroups));
+                } else {
+                    const double *sums = block_sum_groups<NR * ND, RG>(dots);
+                    grid_reduce<NR * ND>(a.red, sums, RG * NR * ND, ND * rhs0, ND * a.nrhs,
+                                         (int)(blockIdx.x / ngroups));
+                }
             }
         }
     }
@@ -329,7 +349,7 @@ __global__ void __launch_bounds__(kDslashMaxBlock) k_dslash(const DslashArgs a)
 // epilogue's reduction the grid holds at most as many blocks as are resident at once (a
 // multiple of the group count, from the occupancy of this instantiation) and blocks
 // stride over the items, so that there is one partial per block and right-hand side.
-template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH>
+template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH, int RG = 1>
 static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
 {
     DslashArgs a = a0;
@@ -340,7 +360,7 @@ static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
     const int bi = bs == 64 ? 0 : bs == 128 ? 1 : 2;
     if (occ[bi] < 0) {
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_dslash<PL, PV, NREAL, NR, EPI, DS, BATCH>, bs, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_dslash<PL, PV, NREAL, NR, EPI, DS, BATCH, RG>, bs, 0) !=
                 cudaSuccess ||
             o < 1)
             o = 1;
@@ -355,8 +375,8 @@ static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
         k_dslash<PL, PV, NREAL, 1, EPI, DS, true><<<items, kDslashBlock, 0, st>>>(a);
         return cudaGetLastError();
     } else {
-        const size_t tiles = ((size_t)a.g.Vh * DS + bs - 1) / bs;
-        const size_t ng = (size_t)(a.nrhs / NR);
+        const size_t tiles = ((size_t)a.g.Vh * DS * RG + bs - 1) / bs;
+        const size_t ng = (size_t)(a.nrhs / (NR * RG));
         const size_t items = tiles * ng;
         const size_t resident = std::max<size_t>(ng, (size_t)std::max(1, a.sm_count) * occ[bi] / ng * ng);
         const size_t blocks = a.red.partials ? std::min(items, resident) : items;
@@ -364,20 +384,33 @@ static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
         a.items = (uint32_t)items;
         a.red.nblocks = (int)(blocks / ng); // partials per right-hand side
         a.red.ntotal = (int)blocks;
-        k_dslash<PL, PV, NREAL, NR, EPI, DS, false><<<(unsigned)blocks, bs, 0, st>>>(a);
+        k_dslash<PL, PV, NREAL, NR, EPI, DS, false, RG><<<(unsigned)blocks, bs, 0, st>>>(a);
         return cudaGetLastError();
     }
 }
 
 template <int PL, int PV, int NREAL, int EPI, int DS>
-static cudaError_t launch_nr(const DslashArgs &a, int nr, cudaStream_t st)
+static cudaError_t launch_nr(const DslashArgs &a, int nr, int rg, cudaStream_t st)
 {
-    if (a.nrhs < 1 || a.nrhs % nr) return cudaErrorInvalidValue;
+    if (a.nrhs < 1 || a.nrhs % (nr * rg)) return cudaErrorInvalidValue;
     if (a.batch) { // one right-hand side per lattice, storage order
-        if (nr != 1 || a.zt || a.nrhs != a.batch_n) return cudaErrorInvalidValue;
+        if (nr != 1 || rg != 1 || a.zt || a.nrhs != a.batch_n) return cudaErrorInvalidValue;
         return launch_one<PL, PV, NREAL, 1, EPI, DS, true>(a, st);
     }
     if (a.zt && !a.g.zt_ok) return cudaErrorInvalidValue;
+    if (rg != 1) { // groups of right-hand sides on one site's threads: one thread per site only
+        if constexpr (DS == 1) {
+            switch (rg * 16 + nr) {
+            case 2 * 16 + 1: return launch_one<PL, PV, NREAL, 1, EPI, 1, false, 2>(a, st);
+            case 2 * 16 + 2: return launch_one<PL, PV, NREAL, 2, EPI, 1, false, 2>(a, st);
+            case 2 * 16 + 4: return launch_one<PL, PV, NREAL, 4, EPI, 1, false, 2>(a, st);
+            case 4 * 16 + 1: return launch_one<PL, PV, NREAL, 1, EPI, 1, false, 4>(a, st);
+            case 4 * 16 + 2: return launch_one<PL, PV, NREAL, 2, EPI, 1, false, 4>(a, st);
+            case 4 * 16 + 4: return launch_one<PL, PV, NREAL, 4, EPI, 1, false, 4>(a, st);
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (nr) {
     case 1: return launch_one<PL, PV, NREAL, 1, EPI, DS, false>(a, st);
     case 2: return launch_one<PL, PV, NREAL, 2, EPI, DS, false>(a, st);
@@ -390,37 +423,38 @@ static cudaError_t launch_nr(const DslashArgs &a, int nr, cudaStream_t st)
 }
 
 template <int PL, int PV, int NREAL, int EPI>
-static cudaError_t launch_ds(const DslashArgs &a, int nr, int ds, cudaStream_t st)
+static cudaError_t launch_ds(const DslashArgs &a, int nr, int ds, int rg, cudaStream_t st)
 {
     switch (ds) {
-    case 1: return launch_nr<PL, PV, NREAL, EPI, 1>(a, nr, st);
-    case 2: return launch_nr<PL, PV, NREAL, EPI, 2>(a, nr, st);
-    case 4: return launch_nr<PL, PV, NREAL, EPI, 4>(a, nr, st);
+    case 1: return launch_nr<PL, PV, NREAL, EPI, 1>(a, nr, rg, st);
+    case 2: return launch_nr<PL, PV, NREAL, EPI, 2>(a, nr, rg, st);
+    case 4: return launch_nr<PL, PV, NREAL, EPI, 4>(a, nr, rg, st);
     }
     return cudaErrorInvalidValue;
 }
 
 template <int PL, int PV, int EPI>
-static cudaError_t launch_prec(const DslashArgs &a, int nreal, int nr, int ds, cudaStream_t st)
+static cudaError_t launch_prec(const DslashArgs &a, int nreal, int nr, int ds, int rg, cudaStream_t st)
 {
     if (nreal == 12) {
         if constexpr (PL == HISQ_F64X) return cudaErrorInvalidValue;
-        else return launch_ds<PL, PV, 12, EPI>(a, nr, ds, st);
+        else return launch_ds<PL, PV, 12, EPI>(a, nr, ds, rg, st);
     }
-    return launch_ds<PL, PV, 18, EPI>(a, nr, ds, st);
+    return launch_ds<PL, PV, 18, EPI>(a, nr, ds, rg, st);
 }
 
 // instantiate the launcher of one link precision with one vector precision
 // (the CG epilogue, EPI = 2, exists for the vector precisions a solver iterates: not 16-bit)
 #define HISQ_DSLASH_INSTANTIATE(PL, PV)                                                                  \
-    cudaError_t dslash_launch_##PL##_##PV(int epi, const DslashArgs &a, int nreal, int nr, int ds,         \
+    cudaError_t dslash_launch_##PL##_##PV(int epi, const DslashArgs &a, int nreal, int nr, int ds, int rg, \
                                           cudaStream_t st)                                               \
     {                                                                                                    \
         if (epi == 2) {                                                                                  \
             if constexpr (PV == HISQ_F16 || PV == HISQ_BF16) return cudaErrorInvalidValue;              \
-            else return launch_prec<PL, PV, 2>(a, nreal, nr, ds, st);                                     \
+            else return launch_prec<PL, PV, 2>(a, nreal, nr, ds, rg, st);                                 \
         }                                                                                                \
-        return epi ? launch_prec<PL, PV, 1>(a, nreal, nr, ds, st) : launch_prec<PL, PV, 0>(a, nreal, nr, ds, st); \
+        return epi ? launch_prec<PL, PV, 1>(a, nreal, nr, ds, rg, st)                                    \
+                   : launch_prec<PL, PV, 0>(a, nreal, nr, ds, rg, st);                                   \
     }
 
 }  // namespace hisq

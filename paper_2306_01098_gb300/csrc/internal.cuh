@@ -194,7 +194,8 @@ struct DslashShape {
     int nr = 1;
     int ds = 1;
     int order = 0; // 0: sites in storage order (t slowest); 1: z and t interchanged in launch order
-    int bs = 128;  // threads per block (sites per block = bs / ds)
+    int bs = 128;  // threads per block (sites per block = bs / (ds rg))
+    int rg = 1;    // groups of right-hand sides sharing one site's threads (ds = 1 only)
 };
 
 // key of a Dslash shape in the context's tuning table: link precision, vector precision and

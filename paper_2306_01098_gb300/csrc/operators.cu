@@ -34,6 +34,7 @@ int apply_mdagm(hisq_ctx *ctx, int prec, double m, const void *in, void *tmp, vo
         sh.ds = it != ctx->tune.end() ? it->second.ds : (ctx->g.Vh < (1u << 20) ? 2 : 1);
         sh.order = it != ctx->tune.end() ? it->second.order : 0;
         sh.bs = it != ctx->tune.end() ? it->second.bs : kDslashBlock;
+        sh.rg = it != ctx->tune.end() ? it->second.rg : 1;
     }
     DslashArgs a = make_dslash_args(ctx, prec, 1, in, tmp, nrhs, rhs_bytes);
     cudaError_t e = dslash_launch(prec, pv, 0, a, L.nreal, sh, st);

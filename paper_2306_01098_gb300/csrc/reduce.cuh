@@ -213,13 +213,47 @@ __device__ __forceinline__ void block_sum_multi(double (&x)[NV])
     }
 }
 
+// Block sums of NV doubles per group of right-hand sides, the group of a thread being
+// lane % RG (RG consecutive lanes share a site, each with its own right-hand sides): lanes of
+// one group are summed across the warp (xor offsets 16 .. RG), then across the warps in a
+// fixed order.  Result in shared memory, value v of group g at out[g * NV + v]; valid for
+// every thread after the call.
+template <int NV, int RG>
+__device__ __forceinline__ const double *block_sum_groups(double (&x)[NV])
+{
+    __shared__ double ws[RG * NV][32];
+    __shared__ double res[RG * NV];
+#pragma unroll
+    for (int o = 16; o >= RG; o >>= 1)
+#pragma unroll
+        for (int v = 0; v < NV; v++) x[v] += __shfl_xor_sync(0xffffffffu, x[v], o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l < RG)
+#pragma unroll
+        for (int v = 0; v < NV; v++) ws[l * NV + v][w] = x[v];
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < RG * NV; k++) {
+            double r = l < nw ? ws[k][l] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+            if (l == 0) res[k] = r;
+        }
+    }
+    __syncthreads();
+    return res;
+}
+
 // Grid reduction of `nval_all` values.  Block (bx, by) supplies the block sums of values
-// [vbase, vbase + nmine) (thread 0 holds them in `mine`) as partial number bx of each;
+// [vbase, vbase + nmine) (thread 0 reads them from `mine`, registers or shared memory) as
+// partial number bx of each; NV is how many values the finishing block sums at once;
 // the last of the R.ntotal blocks to arrive sums the R.nblocks partials of every value
 // in a fixed order and applies R.op.  The counter is reset for the next use.
 template <int NV>
-__device__ __forceinline__ void grid_reduce(const Reduce &R, const double (&mine)[NV], int nmine, int vbase,
-                                            int nval_all, int bx)
+__device__ __forceinline__ void grid_reduce(const Reduce &R, const double *mine, int nmine, int vbase, int nval_all,
+                                            int bx)
 {
     __shared__ bool last;
     if (threadIdx.x == 0) {

@@ -102,6 +102,7 @@ _SIGS = {
     "hisq_mdagm_noalloc": (_I, [_P, _D, _P, _P, _I, _P]),
     "hisq_tune_set": (_I, [_P, _I, _I, _I, _I, _I, _I]),
     "hisq_tune_set_block": (_I, [_P, _I, _I, _I, _I]),
+    "hisq_tune_set_groups": (_I, [_P, _I, _I, _I, _I]),
     "hisq_tune_get": (_I, [_P, _I, _I, _I, ctypes.POINTER(_I)]),
     "hisq_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "hisq_cg": (_I, [_P, _D, _P, _P, _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
@@ -259,9 +260,13 @@ class Context:
     def tune_set_block(self, prec_links, prec_vectors, nrhs, threads_per_block):
         return self.check(lib().hisq_tune_set_block(self.h, prec_links, prec_vectors, nrhs, threads_per_block))
 
+    def tune_set_groups(self, prec_links, prec_vectors, nrhs, rhs_groups):
+        return self.check(lib().hisq_tune_set_groups(self.h, prec_links, prec_vectors, nrhs, rhs_groups))
+
     def tune_get(self, prec_links, prec_vectors, nrhs):
-        """(n_inner, threads_per_site, site_order, threads_per_block) stored for the key, or None."""
-        sh = (ctypes.c_int * 4)()
+        """(n_inner, threads_per_site, site_order, threads_per_block, rhs_groups) stored for the
+        key, or None."""
+        sh = (ctypes.c_int * 5)()
         rc = lib().hisq_tune_get(self.h, prec_links, prec_vectors, nrhs, sh)
         return tuple(sh) if rc == OK else None
 

@@ -368,3 +368,23 @@ def test_persistent_barrier_wait_is_bounded():
     rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, persistent=2)
     assert rc == hisq.OK
     assert true_res(dims, fat, lng, m, b.cpu().numpy(), x.cpu().numpy()) <= 1e-10
+
+
+@pytest.mark.parametrize("sloppy,nr,rg", [(hisq.F32, 2, 4), (hisq.F16, 1, 4), (hisq.F32, 4, 2)])
+def test_multi_rhs_cg_with_rhs_groups(sloppy, nr, rg):
+    # multi-RHS CG whose sloppy Dslash runs groups of right-hand sides on one site's threads:
+    # the D_eo epilogue's per-right-hand-side reductions go through the group-wise block sums
+    dims, m, nrhs = (6, 6, 6, 8), 0.05, 8
+    ctx, fat, lng = setup(dims, 0.5, 1010)
+    pv = hisq.F32
+    ctx.tune_set(sloppy, pv, nrhs, nr, 1)
+    ctx.tune_set_groups(sloppy, pv, nrhs, rg)
+    b = fields.gaussian_source(dims, 2155, nrhs)
+    x = torch.zeros_like(b).cuda()
+    res_out = torch.zeros(nrhs, dtype=torch.float64)
+    rc, st = ctx.cg(m, b.cuda(), x, tol=1e-10, prec_sloppy=sloppy, prec_precise=hisq.F64, residuals=res_out)
+    assert rc == hisq.OK
+    xg = x.cpu().numpy()
+    for r in range(nrhs):
+        assert true_res(dims, fat, lng, m, b[r].numpy(), xg[r]) <= 1e-10
+    _cache.clear()

@@ -120,8 +120,8 @@ def test_dslash_multi_rhs(nrhs, prec):
 
 @pytest.mark.parametrize("prec", [hisq.F64, hisq.F64X, hisq.F32, hisq.F16, hisq.BF16])
 def test_dslash_every_launch_shape(prec):
-    # every (right-hand sides per thread, threads per site, threads per block) shape gives the
-    # same operator
+    # every (right-hand sides per thread, threads per site, right-hand-side groups per site,
+    # threads per block) shape gives the same operator
     dims, nrhs = (6, 4, 4, 8), 8
     ctx, fat, lng = setup(dims)
     x = fields.gaussian_source(dims, 170, nrhs)
@@ -131,20 +131,23 @@ def test_dslash_every_launch_shape(prec):
     for nr in (1, 2, 4, 8):
         if nr == 8 and prec in (hisq.F64, hisq.F64X):
             continue
-        for ds in (1, 2, 4):
+        for ds, rg in ((1, 1), (2, 1), (4, 1), (1, 2), (1, 4)):
+            if rg > 1 and (nr > 4 or nrhs % (nr * rg)):
+                continue
             for bs in (64, 128, 256):
                 ctx.tune_set(prec, pv, nrhs, nr, ds)
                 ctx.tune_set_block(prec, pv, nrhs, bs)
+                ctx.tune_set_groups(prec, pv, nrhs, rg)
                 got_shape = ctx.tune_get(prec, pv, nrhs)
-                assert got_shape[0] == nr and got_shape[1] == ds and got_shape[3] == bs
+                assert got_shape[0] == nr and got_shape[1] == ds and got_shape[3] == bs and got_shape[4] == rg
                 out = torch.full_like(x, float("nan")).cuda()
                 ctx.dslash(0, x.cuda(), out, prec=prec)
                 got = out.cpu().numpy()
                 for r in range(nrhs):
                     if tol is None:
-                        assert site_rel(got[r], want[r]) <= 1e-13, (nr, ds, bs, r)
+                        assert site_rel(got[r], want[r]) <= 1e-13, (nr, ds, rg, bs, r)
                     else:
-                        assert field_rel(got[r], want[r]) <= tol, (nr, ds, bs, r)
+                        assert field_rel(got[r], want[r]) <= tol, (nr, ds, rg, bs, r)
     _cache.clear()
 
 
@@ -418,3 +421,27 @@ def test_float_pair_range(scale):
         ctx.dslash(p, x.cuda(), out, prec=hisq.F64X)
         want = oracle.dslash(dims, fat, lng, x, p)
         assert site_rel(out.cpu().numpy(), want) <= 1e-13, (scale, p)
+
+
+@pytest.mark.parametrize("prec", [hisq.F64, hisq.F32])
+@pytest.mark.parametrize("nr,rg", [(1, 4), (2, 4), (4, 2), (2, 2)])
+def test_mdagm_rhs_groups(prec, nr, rg):
+    # the normal operator's epilogue and its per-right-hand-side dot products with groups of
+    # right-hand sides sharing a site's threads (8 right-hand sides, ragged half volume)
+    dims, m, nrhs = (6, 4, 8, 10), 0.07, 8
+    ctx, fat, lng = setup(dims, precs=(hisq.F64, hisq.F32))
+    ctx.tune_set(prec, prec, nrhs, nr, 1)
+    ctx.tune_set_groups(prec, prec, nrhs, rg)
+    b = fields.gaussian_source(dims, 195, nrhs)
+    out = torch.full_like(b, float("nan")).cuda()
+    ctx.mdagm(m, b.cuda(), out, prec=prec)
+    want = oracle.mdagm(dims, fat, lng, m, b)
+    got = out.cpu().numpy()
+    for r in range(nrhs):
+        if prec == hisq.F64:
+            assert site_rel(got[r], want[r]) <= 1e-13, r
+        else:
+            assert field_rel(got[r], want[r]) <= 2e-6, r
+    with pytest.raises(hisq.HisqError):
+        ctx.tune_set_groups(prec, prec, nrhs, 3)
+    _cache.clear()
