@@ -468,7 +468,7 @@ def run_ours(args, world, rank, local):
                    "l2": "flushed between timed solves (256 MB write)",
                    "l2_persist_links": {-1: "auto", 0: "off", 1: "on"}[args.l2_persist],
                    "sloppy_link_reals": reals,
-                   "iteration_loop": (f"one persistent cooperative kernel per phase ({st.persistent_ds} threads/site)"
+                   "iteration_loop": (f"one persistent cooperative kernel per phase (launch shape {st.persistent_ds})"
                                       if persistent else
                                       "CUDA graph WHILE node" if args.use_graph else "direct launches"),
                    "reductions_per_iteration": 1 if single else 2,
@@ -512,7 +512,7 @@ def main():
     ap.add_argument("--use-graph", type=int, default=1, help="0: direct launches (for ncu launch lists)")
     ap.add_argument("--single-reduction", type=int, default=0, help="1: one grid reduction per CG iteration")
     ap.add_argument("--persistent", type=int, default=-1,
-                    help="-1: the library's choice; 0: multi-kernel loop; 1, 2, 4: persistent kernel, threads per site")
+                    help="-1: the library's choice; 0: multi-kernel loop; 1 to 5: persistent kernel, launch shape")
     ap.add_argument("--sloppy-reals", type=int, default=18, choices=[18, 12], help="sloppy link compression")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -236,12 +236,12 @@ typedef struct {
                               each owning a range of sites whose x, r, p and Ap stay in
                               shared memory, bounded grid-wide barriers between the steps.
                               Used when the range fits (Vh up to about 2100 sites per SM).
-                              -1 (default): when eligible, launch shape 2; 0: never; 1 to 4:
+                              -1 (default): when eligible, launch shape 2; 0: never; 1 to 5:
                               when eligible, with that launch shape (threads per block and
                               load scheduling: 1 = 1024, 2 = 512 with the four hops of a
-                              direction loaded before their products, 3 = 896 and 4 = 1024
-                              likewise).  A barrier wait that runs out (about 1 s) ends the
-                              launch early and the solve returns HISQ_EDEVICE               */
+                              direction loaded before their products, 3 = 896, 4 = 1024 and
+                              5 = 448 likewise).  A barrier wait that runs out (about 1 s)
+                              ends the launch early and the solve returns HISQ_EDEVICE      */
     int selftest_wait;     /* 1: test of that bounded wait: in the first persistent launch one
                               block leaves without arriving at the first barrier, whose wait
                               (bounded to 1 ms here) runs out in every other block; the
@@ -452,7 +452,9 @@ typedef struct hisq_dd hisq_dd;
  * opts->links_on_device; opts->links_phased must be 0; opts->device selects the GPU).  The
  * library copies the slab's links and the time-direction links of the three slices below
  * it, folds in the MILC phases and the antiperiodic time boundary by global position, and
- * keeps them in FP64; the caller keeps ownership.  HISQ_EINVAL for bad dims or slab bounds. */
+ * keeps them in FP64; the caller keeps ownership.  Host links are staged on the device for
+ * the call (2 x 4 V x 144 bytes, freed before it returns).  HISQ_EINVAL for bad dims or slab
+ * bounds. */
 int hisq_dd_create(hisq_dd **dd, const int gdims[4], int t0, int lt, const double *fat, const double *lng,
                    const hisq_opts *opts);
 void hisq_dd_destroy(hisq_dd *dd);

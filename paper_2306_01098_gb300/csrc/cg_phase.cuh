@@ -269,17 +269,14 @@ inline uint32_t phase_chunk(uint32_t Vh, int sms)
 template <int PL, int NREAL, int NT, bool PF>
 static cudaError_t launch_phase_t(const PhaseArgs &a0, int sms, cudaStream_t st)
 {
-    static bool attr = false;
     PhaseArgs a = a0;
     a.chunk = phase_chunk(a.Vh, sms);
     if (a.chunk == 0 || sms > NT || sms > kPhaseMaxBlocks) return cudaErrorInvalidConfiguration;
     const size_t smem = (size_t)a.chunk * kPhaseSmemPerSite + 4 * sizeof(double) * (size_t)sms;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_cg_phase<PL, NREAL, NT, PF>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kPhaseMaxSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // a per-device attribute of the function: set for the current device at every launch
+    cudaError_t e0 = cudaFuncSetAttribute(k_cg_phase<PL, NREAL, NT, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kPhaseMaxSmem);
+    if (e0 != cudaSuccess) return e0;
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_phase<PL, NREAL, NT, PF>, NT, smem);
     if (e != cudaSuccess) return e;
