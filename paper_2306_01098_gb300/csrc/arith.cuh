@@ -326,13 +326,14 @@ struct FloatArith {
 #pragma unroll
         for (int i = 0; i < 6; i++) o.v[i] = fmaf(m, p.v[i], -o.v[i]);
     }
-    __device__ static double dot(const Vec &p, const Acc &o)
+    __device__ static float dotf(const Vec &p, const Acc &o)
     {
         float d = 0.f;
 #pragma unroll
         for (int i = 0; i < 6; i++) d = fmaf(p.v[i], o.v[i], d);
-        return (double)d;
+        return d;
     }
+    __device__ static double dot(const Vec &p, const Acc &o) { return (double)dotf(p, o); }
 };
 
 template <> struct Prec<HISQ_F32> : FloatArith {

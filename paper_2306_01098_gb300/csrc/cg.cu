@@ -158,6 +158,8 @@ void SolverWork::release()
     st = nullptr;
     if (ev) cudaEventDestroy(ev);
     ev = nullptr;
+    if (ev_sc) cudaEventDestroy(ev_sc);
+    ev_sc = nullptr;
 }
 
 int SolverWork::alloc(hisq_ctx *ctx, char **ptr, size_t bytes)
@@ -246,7 +248,8 @@ int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out)
         cudaMallocHost(&W.h_status, sizeof(DevStatus)) != cudaSuccess)
         return set_error(ctx, HISQ_ENOMEM, "pinned scalars");
     if (cudaStreamCreateWithFlags(&W.st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&W.ev, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&W.ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&W.ev_sc, cudaEventDisableTiming) != cudaSuccess)
         return set_error(ctx, HISQ_ECUDA, "solver stream");
     *out = w;
     return HISQ_OK;
@@ -344,7 +347,6 @@ static int sloppy_dslash_pair(hisq_ctx *ctx, SolverWork &w, double m, cudaStream
                               bool fused = false, unsigned long long cond = 0)
 {
     const LinkStore &L = ctx->links[w.ps];
-    const int nr = w.shape.nr;
     DslashArgs a = make_dslash_args(ctx, w.ps, 1, w.p, w.t, w.nrhs, w.rbS);
     a.skip = w.sc;
     if (evs) cudaEventRecord(evs[0], st);
@@ -464,9 +466,11 @@ static int persistent_ds(hisq_ctx *ctx, const SolverWork &w, const hisq_solve_op
     return 2;
 }
 
-// the sloppy iterations of one phase (at most cap) in one cooperative launch
-static int launch_persistent_phase(hisq_ctx *ctx, SolverWork &w, double m, int cap, int ds, int selftest,
-                                   cudaStream_t st)
+// the sloppy iterations of one phase (at most cap, and none once Scalars.it_all reaches
+// it_end) in one cooperative launch; reortho: the launch first re-orthogonalises p against
+// the r of the reliable update before it
+static int launch_persistent_phase(hisq_ctx *ctx, SolverWork &w, double m, int cap, int it_end, int ds, int reortho,
+                                   int selftest, cudaStream_t st)
 {
     PhaseArgs a{};
     a.doe = make_dslash_args(ctx, w.ps, 1, w.p, w.t, 1, w.rbS);
@@ -482,6 +486,8 @@ static int launch_persistent_phase(hisq_ctx *ctx, SolverWork &w, double m, int c
     a.slots = static_cast<PhaseSlot *>(w.phase_slots);
     a.status = ctx->status;
     a.cap = cap;
+    a.it_end = it_end;
+    a.reortho = reortho;
     a.selftest = selftest;
     a.wait_ns = selftest ? 1000000ull : 1000000000ull;
     HISQ_CUDA(ctx, cudaMemsetAsync(w.phase_slots, 0, sizeof(PhaseSlot) * kPhaseMaxBlocks, st));
@@ -493,7 +499,6 @@ static int launch_persistent_phase(hisq_ctx *ctx, SolverWork &w, double m, int c
     case HISQ_BF16: e = phase_launch_HISQ_BF16(a, nreal, ds, ctx->sm_count, st); break;
     }
     if (e != cudaSuccess) return cuda_error(ctx, e, "persistent CG phase launch");
-    HISQ_CUDA(ctx, cudaMemcpyAsync(w.h_status, ctx->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     return HISQ_OK;
 }
 
@@ -615,43 +620,106 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
         it_all = w.h_sc[0].it_all;
     }
     const int it_start = it_all;
-    // Phases: a phase runs iterations until every right-hand side pauses or converges, or
-    // until its cap (the next scheduled reliable update, maxiter, or check_interval for
-    // direct launches); then the host looks at the scalars once.
+    // reliable update: x_hi += x_lo, r_hi = b - A_precise x_hi, scalars, r = sloppy(r_hi)
+    auto queue_ru = [&]() -> int {
+        dispatch(w.pv, [&](auto T) { decltype(T)::accum_hi(w, st); });
+        int e = precise_residual(ctx, w, m, st, w.pp);
+        if (e) return e;
+        k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_RU, tol2, delta2);
+        dispatch(w.pv, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
+        kernels += 5 + (w.pp == HISQ_F64X ? 1 : 0);
+        return HISQ_OK;
+    };
+    // certify a solve the float-pair operator found converged with the FP64 operator
+    auto certify = [&](bool &any) -> int {
+        int e = precise_residual(ctx, w, m, st, HISQ_F64);
+        if (e) return e;
+        k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_RU, tol2, delta2);
+        dispatch(w.pv, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
+        kernels += 5;
+        if ((e = read_scalars(ctx, w, st))) return e;
+        for (int r = 0; r < nrhs; r++) any |= w.h_sc[r].active != 0;
+        return HISQ_OK;
+    };
+    if (pds && !done && o.maxiter > 0) {
+        // Persistent phases, pipelined: every phase ends in a reliable update, and the next
+        // phase (which starts with the re-orthogonalisation of p) is queued behind that
+        // update's read-back of the scalars before the host looks at them, so the GPU does
+        // not wait for the host between phases.  The device bounds each phase itself (the reliable
+        // interval, the iteration budget it_end, convergence), so the phase queued after the
+        // last update runs no iteration; only the next reliable update waits for the host.
+        const int it_end = it_start + o.maxiter;
+        int slot = 0;           // pair of timing events of the phase being queued
+        bool need_phase = true; // no phase is queued behind the last update
+        bool first = true;
+        auto queue_phase = [&](bool reortho) -> int {
+            if (prof) HISQ_CUDA(ctx, cudaEventRecord(w.prof[2 * slot], st));
+            int e = launch_persistent_phase(ctx, w, m, interval, it_end, pds, reortho ? 1 : 0,
+                                            first ? o.selftest_wait : 0, st);
+            if (e) return e;
+            if (prof) HISQ_CUDA(ctx, cudaEventRecord(w.prof[2 * slot + 1], st));
+            kernels++;
+            first = false;
+            return HISQ_OK;
+        };
+        for (;;) {
+            if (need_phase && (rc = queue_phase(!first))) return rc;
+            const int done_slot = slot;
+            if ((rc = queue_ru())) return rc;
+            HISQ_CUDA(ctx, cudaMemcpyAsync(w.h_sc, w.sc, sizeof(Scalars) * w.nrhs, cudaMemcpyDeviceToHost, st));
+            HISQ_CUDA(ctx, cudaMemcpyAsync(w.h_status, ctx->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+            HISQ_CUDA(ctx, cudaEventRecord(w.ev_sc, st));
+            slot ^= 1;
+            if ((rc = queue_phase(true))) return rc; // the next phase, before the host decides
+            HISQ_CUDA(ctx, cudaEventSynchronize(w.ev_sc));
+            if (w.h_status->error) {
+                cudaStreamSynchronize(st);
+                cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), st);
+                cudaStreamSynchronize(st);
+                return set_error(ctx, HISQ_EDEVICE, "a grid-barrier wait of the persistent CG kernel ran out");
+            }
+            const int executed = w.h_sc[0].it_all - it_all;
+            it_all = w.h_sc[0].it_all;
+            if (prof) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, w.prof[2 * done_slot], w.prof[2 * done_slot + 1]) == cudaSuccess) {
+                    pms += ms;
+                    piters += executed;
+                    plaunch++;
+                }
+            }
+            const int it = w.h_sc[0].iters;
+            dcalls += 2L * (it - prev_iters);
+            prev_iters = it;
+            nru++;
+            bool any = w.h_sc[0].active != 0;
+            const bool last = it_all - it_start >= o.maxiter;
+            need_phase = false;
+            if (!any && w.pp != HISQ_F64 && ctx->links[HISQ_F64].built) {
+                // the queued phase has run no iteration (nothing was active); if the FP64
+                // residual is above the tolerance the solve goes on with a fresh phase
+                if ((rc = certify(any))) return rc;
+                need_phase = true;
+            }
+            if (!any || last) break;
+        }
+        done = true;
+    }
+    // Phases of the multi-kernel loop: a phase runs iterations until every right-hand side
+    // pauses or converges, or until its cap (the next scheduled reliable update, maxiter, or
+    // check_interval for direct launches); then the host looks at the scalars once.
     while (!done) {
         const int budget = o.maxiter - (it_all - it_start);
         if (budget <= 0) break;
         int cap = std::min(interval - since_ru, budget);
-        if (!o.use_graph && !pds) cap = std::min(cap, ci);
+        if (!o.use_graph) cap = std::min(cap, ci);
         // Sampled timing (multi-kernel loop): the phase's first two iterations run as direct
         // launches and the second one's Dslash pair is timed; queued behind the first, its
         // launches start back to back on the GPU, so the events hold no host launch gaps.
         // Taken only when the phase may run three or more iterations; kept only if both did
-        // work.  The persistent kernel is timed as a whole launch instead.
-        const bool sample = prof && cap >= 3 && !pds;
-        // reliable update: x_hi += x_lo, r_hi = b - A_precise x_hi, scalars, r = sloppy(r_hi)
-        auto queue_ru = [&]() -> int {
-            dispatch(w.pv, [&](auto T) { decltype(T)::accum_hi(w, st); });
-            int e = precise_residual(ctx, w, m, st, w.pp);
-            if (e) return e;
-            k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_RU, tol2, delta2);
-            dispatch(w.pv, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
-            kernels += 5 + (w.pp == HISQ_F64X ? 1 : 0);
-            return HISQ_OK;
-        };
-        bool ru_queued = false;
-        if (pds) {
-            // every iteration of the phase in one cooperative launch
-            if (prof) HISQ_CUDA(ctx, cudaEventRecord(w.prof[0], st));
-            if ((rc = launch_persistent_phase(ctx, w, m, cap, pds, o.selftest_wait, st))) return rc;
-            if (prof) HISQ_CUDA(ctx, cudaEventRecord(w.prof[1], st));
-            kernels++;
-            // a persistent phase always ends in a reliable update (a pause, convergence, the
-            // interval cap or the iteration budget): queue it before looking at the scalars,
-            // which the update leaves as the phase left them apart from the residual state
-            if ((rc = queue_ru())) return rc;
-            ru_queued = true;
-        } else if (o.use_graph) {
+        // work.
+        const bool sample = prof && cap >= 3;
+        if (o.use_graph) {
             k_phase_begin<<<1, 1, 0, st>>>(w.ctl, w.sc, cap);
             kernels++;
             if (sample) {
@@ -676,26 +744,10 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
                 if ((rc = launch_iteration(ctx, w, m, st, (sample && i == 1) ? &w.prof[0] : nullptr, 0))) return rc;
         }
         if ((rc = read_scalars(ctx, w, st))) return rc;
-        if (pds && w.h_status->error) {
-            cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), st);
-            cudaStreamSynchronize(st);
-            return set_error(ctx, HISQ_EDEVICE, "a grid-barrier wait of the persistent CG kernel ran out");
-        }
         const int executed = w.h_sc[0].it_all - it_all; // iterations the device ran in this phase
         it_all = w.h_sc[0].it_all;
         since_ru += executed;
-        if (pds) {
-            if (prof) {
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, w.prof[0], w.prof[1]) == cudaSuccess) {
-                    pms += ms;
-                    piters += executed;
-                    plaunch++;
-                }
-            }
-        } else {
-            kernels += per_it * executed - (o.use_graph && sample ? 2 * per_it : 0);
-        }
+        kernels += per_it * executed - (o.use_graph && sample ? 2 * per_it : 0);
         int it = 0;
         bool any_active = false, any_flag = false;
         for (int r = 0; r < nrhs; r++) {
@@ -716,24 +768,15 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
             }
         }
         const bool last = it_all - it_start >= o.maxiter;
-        if (ru_queued || any_flag || since_ru >= interval || !any_active || last) {
-            if (!ru_queued) {
-                if ((rc = queue_ru())) return rc;
-                if ((rc = read_scalars(ctx, w, st))) return rc;
-            }
+        if (any_flag || since_ru >= interval || !any_active || last) {
+            if ((rc = queue_ru())) return rc;
+            if ((rc = read_scalars(ctx, w, st))) return rc;
             nru++;
             since_ru = 0;
             bool any = false;
             for (int r = 0; r < nrhs; r++) any |= w.h_sc[r].active != 0;
-            if (!any && w.pp != HISQ_F64 && ctx->links[HISQ_F64].built) {
-                // converged by the float-pair operator: certify with the FP64 operator
-                if ((rc = precise_residual(ctx, w, m, st, HISQ_F64))) return rc;
-                k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_RU, tol2, delta2);
-                dispatch(w.pv, [&](auto T) { decltype(T)::from_hi(w, w.r, st); });
-                kernels += 5;
-                if ((rc = read_scalars(ctx, w, st))) return rc;
-                for (int r = 0; r < nrhs; r++) any |= w.h_sc[r].active != 0;
-            }
+            // converged by the float-pair operator: certify with the FP64 operator
+            if (!any && w.pp != HISQ_F64 && ctx->links[HISQ_F64].built && (rc = certify(any))) return rc;
             if (!any || last) break;
             dispatch(w.pv, [&](auto T) { decltype(T)::reortho(w, st); });
             kernels += 2;

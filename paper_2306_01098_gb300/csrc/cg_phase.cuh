@@ -62,8 +62,10 @@ struct PhaseArgs {
     PhaseSlot *slots;     // one per block, zeroed before the launch
     DevStatus *status;    // device error flag
     int cap;              // iterations this launch may run
+    int it_end;           // and no iteration once Scalars.it_all reaches this (the solve's budget)
     unsigned long long wait_ns; // bound on one barrier wait
     int selftest;         // block 0 ends at once without arriving: the others' first wait runs out
+    int reortho;          // the launch follows a reliable update: re-orthogonalise p against r first
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
@@ -173,7 +175,72 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
     const uint32_t G = gridDim.x;
     unsigned g = 0; // grid barriers passed
     bool ok = true;
-    for (int it = 0; ok && it < a.cap && S.active; it++) {
+    // After a reliable update replaced r: remove from p its component along r, then
+    // p = r + beta p, i.e. p = (1 - beta <r,p>/|r|^2) r + beta p with the complex
+    // <r,p> = sum conj(r) p over the lattice: per-site products in FP32, float-float sums in
+    // the block, block partials through the barrier's records (summed in the same order by
+    // every block), the coefficients in FP64 and the update in FP32 like the iterations'.
+    if (a.reortho && S.active) {
+        FF d[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        for (uint32_t s = cbeg + threadIdx.x; s < cend; s += NT) {
+            typename B::Vec pv, rv;
+            T::load_coh(sp, s - cbeg, pv);
+            T::load_coh(sr, s - cbeg, rv);
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                re = fmaf(rv.v[2 * i], pv.v[2 * i], fmaf(rv.v[2 * i + 1], pv.v[2 * i + 1], re));
+                im = fmaf(rv.v[2 * i], pv.v[2 * i + 1], fmaf(-rv.v[2 * i + 1], pv.v[2 * i], im));
+            }
+            ff_add(d[0], re);
+            ff_add(d[1], im);
+        }
+        block_sum_ff<2>(d);
+        double mine[4] = {0.0, 0.0, 0.0, 0.0};
+        if (threadIdx.x == 0) {
+            mine[0] = ff_value(d[0]);
+            mine[1] = ff_value(d[1]);
+        }
+        ok = grid_barrier(a.slots, ++g, mine, a.status, a.wait_ns, spart);
+        if (ok) {
+            if (threadIdx.x < 32) {
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    double acc = 0.0;
+                    for (uint32_t i = threadIdx.x; i < G; i += 32) acc += spart[j * G + i];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+                    if (threadIdx.x == 0) tot[j] = acc;
+                }
+            }
+            __syncthreads();
+            const double beta = S.beta, rr = S.rr;
+            const float cre = (float)(rr > 0.0 ? 1.0 - beta * tot[0] / rr : 1.0);
+            const float cim = (float)(rr > 0.0 ? -beta * tot[1] / rr : 0.0);
+            const float bf = (float)beta;
+            for (uint32_t s = cbeg + threadIdx.x; s < cend; s += NT) {
+                typename B::Vec pv, rv, out;
+                T::load_coh(sp, s - cbeg, pv);
+                T::load_coh(sr, s - cbeg, rv);
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    const float xr = rv.v[2 * i], xi = rv.v[2 * i + 1], yr = pv.v[2 * i], yi = pv.v[2 * i + 1];
+                    out.v[2 * i] = fmaf(cre, xr, fmaf(-cim, xi, bf * yr));
+                    out.v[2 * i + 1] = fmaf(cre, xi, fmaf(cim, xr, bf * yi));
+                }
+                B::store(sp, s - cbeg, out);
+                B::store(a.p, s, out);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                S.last = tot[0];
+                S.last_im = tot[1];
+            }
+            // p complete everywhere before the first D_oe gathers it
+            ok = grid_barrier(a.slots, ++g, nullptr, a.status, a.wait_ns);
+        }
+    }
+    for (int it = 0; ok && it < a.cap && S.it_all < a.it_end && S.active; it++) {
         // t = D_oe p (p gathered from global memory)
         {
             double none[1] = {0.0};
@@ -184,15 +251,19 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
         }
         if (!(ok = grid_barrier(a.slots, ++g, nullptr, a.status, a.wait_ns))) break;
         // Ap = m4 p - D_eo t into shared memory, with the four dot products of the
-        // single-reduction step; the block sums travel with the barrier's arrival record
+        // single-reduction step (per-site products in FP32, float-float sums in the block);
+        // the block sums travel with the barrier's arrival record
         {
-            double d[4] = {0.0, 0.0, 0.0, 0.0};
+            FF d[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             for (uint32_t s = cbeg + threadIdx.x; s < cend; s += NT)
-                dslash_item<PL, HISQ_F32, NREAL, 1, 2, 1, true, PF>(a.deo, a.deo.g, a.deo.links, a.deo.slot_bytes,
-                                                                    a.deo.scale[0], a.deo.scale[1], a.deo.in, sAp, sp,
-                                                                    sr, nullptr, 0u, d, s, cbeg);
-            block_sum_multi<4>(d);
-            if (!(ok = grid_barrier(a.slots, ++g, d, a.status, a.wait_ns, spart))) break;
+                dslash_item<PL, HISQ_F32, NREAL, 1, 2, 1, true, PF, 1, FF>(
+                    a.deo, a.deo.g, a.deo.links, a.deo.slot_bytes, a.deo.scale[0], a.deo.scale[1], a.deo.in, sAp, sp,
+                    sr, nullptr, 0u, d, s, cbeg);
+            block_sum_ff<4>(d);
+            double mine[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) mine[j] = threadIdx.x == 0 ? ff_value(d[j]) : 0.0;
+            if (!(ok = grid_barrier(a.slots, ++g, mine, a.status, a.wait_ns, spart))) break;
         }
         // the same totals in every block: lane i sums the partials of blocks i, i + 32, ...
         // (copied to shared memory by the barrier) then a fixed tree
@@ -212,7 +283,8 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
             S.last_im = tot[1];
             S.last = tot[2];
             fin_ab(S, tot[3]);
-            mode = it + 1 >= a.cap ? 1 : 0; // last iteration of the launch: p is left to the host
+            // last iteration of the launch: p is left to the re-orthogonalisation after the update
+            mode = it + 1 >= a.cap || S.it_all >= a.it_end ? 1 : 0;
         }
         __syncthreads();
         // x += alpha p ; r -= alpha Ap ; p = r + beta p  (alpha only if this iteration made it);
@@ -243,7 +315,7 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
             }
         }
         // p complete everywhere before the next D_oe gathers it
-        if (it + 1 < a.cap && S.active) ok = grid_barrier(a.slots, ++g, nullptr, a.status, a.wait_ns);
+        if (mode == 0 && S.active) ok = grid_barrier(a.slots, ++g, nullptr, a.status, a.wait_ns);
     }
     // x and r back to global memory (p is there already)
     __syncthreads();

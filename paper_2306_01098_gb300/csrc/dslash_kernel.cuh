@@ -44,6 +44,22 @@ namespace hisq {
 // dot products per right-hand side reduced by an epilogue
 template <int EPI> struct EpiDots { static constexpr int n = EPI == 2 ? 4 : 1; };
 
+// |v|^2 and |o|^2 of FP32 records in float arithmetic, returned as floats
+__device__ __forceinline__ float vec_norm2f(const FloatArith::Vec &v)
+{
+    float d = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; i++) d = fmaf(v.v[i], v.v[i], d);
+    return d;
+}
+__device__ __forceinline__ float acc_norm2f(const FloatArith::Acc &o)
+{
+    float d = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; i++) d = fmaf(o.v[i], o.v[i], d);
+    return d;
+}
+
 // |v|^2 of a vector: float arithmetic for the float types, double otherwise
 template <class T>
 __device__ __forceinline__ double vec_norm2(const typename T::Vec &v)
@@ -105,15 +121,19 @@ __device__ __forceinline__ void vec_load(const char *base, uint32_t s, typename 
 // right-hand sides g NR .. g NR + NR - 1 from the given ones; their loads of the site's links
 // are the same addresses in the same instruction (one request), so a link is fetched once
 // for all NR RG right-hand sides with 1/RG of the accumulators per thread.
-template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool COH = false, bool PF = false, int RG = 1>
+template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool COH = false, bool PF = false, int RG = 1,
+          class DT = double>
 __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, const char *links, size_t slot_bytes,
                                             double sc0, double sc1, const char *in, char *outp, const char *pvp,
                                             const char *rvp, const double *m4r, uint32_t tile,
-                                            double (&dots)[NR * EpiDots<EPI>::n], uint32_t tid = threadIdx.x,
+                                            DT (&dots)[NR * EpiDots<EPI>::n], uint32_t tid = threadIdx.x,
                                             uint32_t ebase = 0)
 {
     static_assert(RG == 1 || DS == 1, "right-hand side groups share a site only with one thread per direction set");
     constexpr int ND = EpiDots<EPI>::n;
+    constexpr bool FFD = std::is_same<DT, FF>::value; // float-float sums (FP32 vectors only)
+    static_assert(!FFD || std::is_same<typename Prec<PV>::Vec, FloatArith::Vec>::value,
+                  "float-float dot sums are for FP32 iteration vectors");
     using T = Prec<PV>;  // vectors and arithmetic
     using TL = Prec<PL>; // link storage
     constexpr int LB = NREAL == 18 ? LinkBytes<PL>::b18 : LinkBytes<PL>::b12;
@@ -247,13 +267,20 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
                 typename T::Vec pv;
                 vec_load<T, COH>(pvp + (size_t)r * a.rhs_bytes, s - ebase, pv);
                 T::mdagm_epilogue(out[r], a.m4 + (m4r ? m4r[r] : 0.0), pv);
-                dots[r * ND] += T::dot(pv, out[r]);
+                if constexpr (FFD) ff_add(dots[r * ND], T::dotf(pv, out[r]));
+                else dots[r * ND] += T::dot(pv, out[r]);
                 if constexpr (EPI == 2) {
                     typename T::Vec rv;
                     vec_load<T, COH>(rvp + (size_t)r * a.rhs_bytes, s - ebase, rv);
-                    dots[r * ND + 1] += vec_norm2<T>(rv);
-                    dots[r * ND + 2] += T::dot(rv, out[r]);
-                    dots[r * ND + 3] += acc_norm2<T>(out[r]);
+                    if constexpr (FFD) {
+                        ff_add(dots[r * ND + 1], vec_norm2f(rv));
+                        ff_add(dots[r * ND + 2], T::dotf(rv, out[r]));
+                        ff_add(dots[r * ND + 3], acc_norm2f(out[r]));
+                    } else {
+                        dots[r * ND + 1] += vec_norm2<T>(rv);
+                        dots[r * ND + 2] += T::dot(rv, out[r]);
+                        dots[r * ND + 3] += acc_norm2<T>(out[r]);
+                    }
                 }
             }
             T::store(outp + (size_t)r * a.rhs_bytes, EPI >= 1 ? s - ebase : s, out[r]);

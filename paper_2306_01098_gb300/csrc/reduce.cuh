@@ -186,6 +186,78 @@ __device__ __forceinline__ void finish_control(const Reduce &R, int nrhs)
     }
 }
 
+// ---------------------------------------------------------------- float-float sums
+// A sum kept as an unevaluated pair of floats h + l, accumulated on the FP32 pipes: on this
+// GPU an FP64 add or conversion costs about as much as sixty FP32 operations, and the dot
+// products of the FP32 iteration vectors are summed over every site each iteration.
+// Adding a float uses Knuth's TwoSum (the exact rounding error of h + x goes into l);
+// merging two pairs is TwoSum on the high parts followed by Dekker's Fast2Sum
+// renormalisation.  The explicit _rn intrinsics keep the compiler from contracting or
+// reassociating the error terms.  The value is (double)h + (double)l, accurate to about
+// 2^-44 relative for sums of non-negative terms and to the usual cancellation bound otherwise.
+struct FF {
+    float h, l;
+};
+
+__device__ __forceinline__ void ff_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void ff_add(FF &a, float x)
+{
+    float s, e;
+    ff_two_sum(a.h, x, s, e);
+    a.h = s;
+    a.l = __fadd_rn(a.l, e);
+}
+
+__device__ __forceinline__ void ff_merge(FF &a, const FF &b)
+{
+    float s, e;
+    ff_two_sum(a.h, b.h, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    a.h = __fadd_rn(s, e);
+    a.l = __fsub_rn(e, __fsub_rn(a.h, s));
+}
+
+__device__ __forceinline__ double ff_value(const FF &a) { return (double)a.h + (double)a.l; }
+
+// block-wide float-float sums of NV values at once (one barrier for all); valid on thread 0
+template <int NV>
+__device__ __forceinline__ void block_sum_ff(FF (&x)[NV])
+{
+    __shared__ FF wsum_ff[NV][32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const FF y = {__shfl_down_sync(0xffffffffu, x[v].h, o), __shfl_down_sync(0xffffffffu, x[v].l, o)};
+            ff_merge(x[v], y);
+        }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0)
+#pragma unroll
+        for (int v = 0; v < NV; v++) wsum_ff[v][w] = x[v];
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            FF r = l < nw ? wsum_ff[v][l] : FF{0.f, 0.f};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const FF y = {__shfl_down_sync(0xffffffffu, r.h, o), __shfl_down_sync(0xffffffffu, r.l, o)};
+                ff_merge(r, y);
+            }
+            x[v] = r;
+        }
+    }
+}
+
 // block-wide sums of NV doubles at once (one barrier for all); results valid on thread 0
 template <int NV>
 __device__ __forceinline__ void block_sum_multi(double (&x)[NV])

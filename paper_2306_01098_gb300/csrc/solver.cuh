@@ -29,6 +29,7 @@ struct SolverWork {
     int nblk_vec = 0, nblk_dslash = 0;
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t ev_sc = nullptr; // the scalars' read-back of a pipelined persistent phase
     cudaGraphExec_t graph = nullptr;
     double graph_m = -1.0;
     bool graph_l2 = false;

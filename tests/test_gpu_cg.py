@@ -353,6 +353,28 @@ def test_persistent_phase_bench_workload():
         ctx.close()
 
 
+@pytest.mark.parametrize("precise", [hisq.F64, hisq.F64X])
+def test_persistent_budget_and_phase_count(precise):
+    # the next phase is queued before the host reads the last update's scalars, so the
+    # iteration budget is enforced on the device: maxiter across several capped phases ends
+    # at exactly maxiter iterations; every timed phase is followed by one reliable update;
+    # a float-pair solve is certified by the FP64 operator as before
+    dims, m = (8, 8, 8, 8), 0.01
+    ctx, fat, lng = setup(dims, 0.5, 1013)
+    b = fields.gaussian_source(dims, 2180)[0].cuda()
+    x = torch.zeros_like(b)
+    rc, st = ctx.cg(m, b, x, tol=1e-10, maxiter=71, prec_sloppy=hisq.F16, prec_precise=precise,
+                    reliable_interval=20, persistent=2, profile=1)
+    assert rc == hisq.ENOTCONVERGED and st.iterations == 71 and st.persistent_ds == 2
+    assert st.phase_iterations == 71 and st.phase_launches == st.reliable_updates
+    x = torch.zeros_like(b)
+    rc, st = ctx.cg(m, b, x, tol=1e-10, prec_sloppy=hisq.F16, prec_precise=precise, reliable_interval=20,
+                    persistent=2, profile=1)
+    assert rc == hisq.OK and st.persistent_ds == 2
+    assert st.phase_iterations == st.iterations and st.phase_launches == st.reliable_updates
+    assert true_res(dims, fat, lng, m, b.cpu().numpy(), x.cpu().numpy()) <= 1e-10
+
+
 def test_persistent_barrier_wait_is_bounded():
     # one block leaves the first launch without arriving at its first grid barrier: every
     # other block's wait runs out after 1 ms, raises the device error flag and ends the
