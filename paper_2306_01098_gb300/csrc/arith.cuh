@@ -320,12 +320,12 @@ struct FloatArith {
 #pragma unroll
         for (int i = 0; i < 6; i++) a.v[i] += __shfl_xor_sync(0xffffffffu, a.v[i], off);
     }
-    __device__ static void mdagm_epilogue(Acc &o, double m4, const Vec &p)
+    __device__ static void mdagm_epilogue(Acc &o, float m, const Vec &p)
     {
-        const float m = (float)m4;
 #pragma unroll
         for (int i = 0; i < 6; i++) o.v[i] = fmaf(m, p.v[i], -o.v[i]);
     }
+    __device__ static void mdagm_epilogue(Acc &o, double m4, const Vec &p) { mdagm_epilogue(o, (float)m4, p); }
     __device__ static float dotf(const Vec &p, const Acc &o)
     {
         float d = 0.f;

@@ -478,6 +478,11 @@ static int launch_persistent_phase(hisq_ctx *ctx, SolverWork &w, double m, int c
     a.deo = make_dslash_args(ctx, w.ps, 0, w.t, w.Ap, 1, w.rbS);
     a.deo.zt = 0;
     a.deo.m4 = 4.0 * m * m;
+    for (DslashArgs *d : {&a.doe, &a.deo}) {
+        d->m4f = (float)d->m4;
+        d->scale_f[0] = (float)d->scale[0];
+        d->scale_f[1] = (float)d->scale[1];
+    }
     a.x = w.xlo;
     a.p = w.p;
     a.r = w.r;

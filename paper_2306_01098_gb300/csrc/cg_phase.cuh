@@ -38,9 +38,10 @@ namespace hisq {
 // ceil(c / NT) passes).
 
 // Arrival record of one block (one 64-byte line): the number of grid barriers it has passed
-// and, at the barrier after the normal operator, its partial sums of the four dot products.
+// and, at the barrier after the normal operator, its partial sums of the four dot products
+// (float-float pairs).
 struct PhaseSlot {
-    double part[4]; // first: 16-byte aligned for the paired loads that copy it
+    FF part[4]; // first: 16-byte aligned for the paired loads that copy it
     unsigned gen;
     unsigned pad;
     double pad2[3];
@@ -102,8 +103,8 @@ __device__ __forceinline__ unsigned long long phase_clock_ns()
 // device error flag raised, if a wait ran out.
 // With spart (shared memory, [4][gridDim.x]), the thread that waited for record i also copies
 // that block's partial sums there, so all of them arrive in one parallel round trip.
-__device__ __forceinline__ bool grid_barrier(PhaseSlot *slots, unsigned g, const double *mine, DevStatus *st,
-                                            unsigned long long limit_ns, double *spart = nullptr)
+__device__ __forceinline__ bool grid_barrier(PhaseSlot *slots, unsigned g, const FF *mine, DevStatus *st,
+                                            unsigned long long limit_ns, FF *spart = nullptr)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -128,12 +129,12 @@ __device__ __forceinline__ bool grid_barrier(PhaseSlot *slots, unsigned g, const
         }
         asm volatile("fence.acq_rel.gpu;" ::: "memory");
         if (spart && good) {
-            const double2 *q = reinterpret_cast<const double2 *>(slots[threadIdx.x].part);
-            const double2 a0 = __ldcg(q), a1 = __ldcg(q + 1);
-            spart[threadIdx.x] = a0.x;
-            spart[gridDim.x + threadIdx.x] = a0.y;
-            spart[2 * gridDim.x + threadIdx.x] = a1.x;
-            spart[3 * gridDim.x + threadIdx.x] = a1.y;
+            const float4 *q = reinterpret_cast<const float4 *>(slots[threadIdx.x].part);
+            const float4 a0 = __ldcg(q), a1 = __ldcg(q + 1);
+            spart[threadIdx.x] = FF{a0.x, a0.y};
+            spart[gridDim.x + threadIdx.x] = FF{a0.z, a0.w};
+            spart[2 * gridDim.x + threadIdx.x] = FF{a1.x, a1.y};
+            spart[3 * gridDim.x + threadIdx.x] = FF{a1.z, a1.w};
         }
     }
     good = __syncthreads_and(good);
@@ -142,6 +143,26 @@ __device__ __forceinline__ bool grid_barrier(PhaseSlot *slots, unsigned g, const
         atomicExch(&st->error, (int)HISQ_EDEVICE);
     }
     return good != 0;
+}
+
+// The same totals in every block: warp j < NV sums value j of the G block partials (copied
+// to shared memory by the barrier), lane i taking blocks i, i + 32, ..., then a fixed tree;
+// float-float throughout, one FP64 conversion per value.  Valid after the call's barrier.
+template <int NV>
+__device__ __forceinline__ void phase_totals(const FF *spart, uint32_t G, double *tot)
+{
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (w < NV) {
+        FF acc = {0.f, 0.f};
+        for (uint32_t i = l; i < G; i += 32) ff_merge(acc, spart[w * G + i]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const FF y = {__shfl_down_sync(0xffffffffu, acc.h, o), __shfl_down_sync(0xffffffffu, acc.l, o)};
+            ff_merge(acc, y);
+        }
+        if (l == 0) tot[w] = ff_value(acc);
+    }
+    __syncthreads();
 }
 
 // PL: sloppy link storage (F32, F16, BF16) with NREAL reals; vectors FP32; NT threads per
@@ -155,12 +176,13 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
     extern __shared__ __align__(16) char phase_smem[];
     __shared__ Scalars S;
     __shared__ double tot[4];
-    __shared__ int mode;
+    __shared__ float coef[3];
+    __shared__ int mode, xr_on;
     if (a.selftest && blockIdx.x == 0) return;
     const uint32_t cbeg = min(a.Vh, blockIdx.x * a.chunk), cend = min(a.Vh, cbeg + a.chunk);
     char *sx = phase_smem, *sr = sx + (size_t)a.chunk * 24, *sp = sr + (size_t)a.chunk * 24;
     char *sAp = sp + (size_t)a.chunk * 24;
-    double *spart = reinterpret_cast<double *>(sAp + (size_t)a.chunk * 24); // [4][gridDim.x]
+    FF *spart = reinterpret_cast<FF *>(sAp + (size_t)a.chunk * 24); // [4][gridDim.x]
     for (uint32_t s = cbeg + threadIdx.x; s < cend; s += NT) {
         typename B::Vec v;
         T::load_coh(a.x, s, v);
@@ -196,28 +218,18 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
             ff_add(d[1], im);
         }
         block_sum_ff<2>(d);
-        double mine[4] = {0.0, 0.0, 0.0, 0.0};
-        if (threadIdx.x == 0) {
-            mine[0] = ff_value(d[0]);
-            mine[1] = ff_value(d[1]);
-        }
+        const FF mine[4] = {d[0], d[1], {0.f, 0.f}, {0.f, 0.f}};
         ok = grid_barrier(a.slots, ++g, mine, a.status, a.wait_ns, spart);
         if (ok) {
-            if (threadIdx.x < 32) {
-#pragma unroll
-                for (int j = 0; j < 2; j++) {
-                    double acc = 0.0;
-                    for (uint32_t i = threadIdx.x; i < G; i += 32) acc += spart[j * G + i];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-                    if (threadIdx.x == 0) tot[j] = acc;
-                }
+            phase_totals<2>(spart, G, tot);
+            if (threadIdx.x == 0) {
+                const double beta = S.beta, rr = S.rr;
+                coef[0] = (float)(rr > 0.0 ? 1.0 - beta * tot[0] / rr : 1.0);
+                coef[1] = (float)(rr > 0.0 ? -beta * tot[1] / rr : 0.0);
+                coef[2] = (float)beta;
             }
             __syncthreads();
-            const double beta = S.beta, rr = S.rr;
-            const float cre = (float)(rr > 0.0 ? 1.0 - beta * tot[0] / rr : 1.0);
-            const float cim = (float)(rr > 0.0 ? -beta * tot[1] / rr : 0.0);
-            const float bf = (float)beta;
+            const float cre = coef[0], cim = coef[1], bf = coef[2];
             for (uint32_t s = cbeg + threadIdx.x; s < cend; s += NT) {
                 typename B::Vec pv, rv, out;
                 T::load_coh(sp, s - cbeg, pv);
@@ -243,11 +255,11 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
     for (int it = 0; ok && it < a.cap && S.it_all < a.it_end && S.active; it++) {
         // t = D_oe p (p gathered from global memory)
         {
-            double none[1] = {0.0};
+            FF none[1] = {{0.f, 0.f}};
             for (uint32_t s = cbeg + threadIdx.x; s < cend; s += NT)
-                dslash_item<PL, HISQ_F32, NREAL, 1, 0, 1, true, PF>(a.doe, a.doe.g, a.doe.links, a.doe.slot_bytes,
-                                                                    a.doe.scale[0], a.doe.scale[1], a.doe.in, a.doe.out,
-                                                                    nullptr, nullptr, nullptr, 0u, none, s);
+                dslash_item<PL, HISQ_F32, NREAL, 1, 0, 1, true, PF, 1, FF>(
+                    a.doe, a.doe.g, a.doe.links, a.doe.slot_bytes, a.doe.scale_f[0], a.doe.scale_f[1], a.doe.in,
+                    a.doe.out, nullptr, nullptr, nullptr, 0u, none, s);
         }
         if (!(ok = grid_barrier(a.slots, ++g, nullptr, a.status, a.wait_ns))) break;
         // Ap = m4 p - D_eo t into shared memory, with the four dot products of the
@@ -257,27 +269,13 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
             FF d[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             for (uint32_t s = cbeg + threadIdx.x; s < cend; s += NT)
                 dslash_item<PL, HISQ_F32, NREAL, 1, 2, 1, true, PF, 1, FF>(
-                    a.deo, a.deo.g, a.deo.links, a.deo.slot_bytes, a.deo.scale[0], a.deo.scale[1], a.deo.in, sAp, sp,
-                    sr, nullptr, 0u, d, s, cbeg);
+                    a.deo, a.deo.g, a.deo.links, a.deo.slot_bytes, a.deo.scale_f[0], a.deo.scale_f[1], a.deo.in, sAp,
+                    sp, sr, nullptr, 0u, d, s, cbeg);
             block_sum_ff<4>(d);
-            double mine[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) mine[j] = threadIdx.x == 0 ? ff_value(d[j]) : 0.0;
-            if (!(ok = grid_barrier(a.slots, ++g, mine, a.status, a.wait_ns, spart))) break;
+            if (!(ok = grid_barrier(a.slots, ++g, d, a.status, a.wait_ns, spart))) break;
         }
-        // the same totals in every block: lane i sums the partials of blocks i, i + 32, ...
-        // (copied to shared memory by the barrier) then a fixed tree
-        if (threadIdx.x < 32) {
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                double acc = 0.0;
-                for (uint32_t i = threadIdx.x; i < G; i += 32) acc += spart[j * G + i];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-                if (threadIdx.x == 0) tot[j] = acc;
-            }
-        }
-        __syncthreads();
+        phase_totals<4>(spart, G, tot);
+        // the scalars (FP64, one thread), then their float images for the update
         if (threadIdx.x == 0) {
             S.pAp = tot[0];
             S.last_im = tot[1];
@@ -285,13 +283,18 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
             fin_ab(S, tot[3]);
             // last iteration of the launch: p is left to the re-orthogonalisation after the update
             mode = it + 1 >= a.cap || S.it_all >= a.it_end ? 1 : 0;
+            const double alpha = alpha_fresh_for_x(S) ? S.alpha : 0.0;
+            coef[0] = (float)alpha;
+            coef[1] = (float)S.beta;
+            xr_on = alpha != 0.0;
         }
         __syncthreads();
-        // x += alpha p ; r -= alpha Ap ; p = r + beta p  (alpha only if this iteration made it);
-        // the new p also goes to global memory for the next D_oe
+        // x += alpha p ; r -= alpha Ap ; p = r + beta p  (alpha only if this iteration made it),
+        // in FP32 like the multi-kernel loop's updates; the new p also goes to global memory
+        // for the next D_oe
         {
-            const double alpha = alpha_fresh_for_x(S) ? S.alpha : 0.0, beta = S.beta;
-            const bool do_xr = alpha != 0.0;
+            const float af = coef[0], bf = coef[1];
+            const bool do_xr = xr_on != 0;
             const bool do_p = mode == 0 && S.active;
             for (uint32_t s = cbeg + threadIdx.x; s < cend; s += NT) {
                 const uint32_t i = s - cbeg;
@@ -302,13 +305,17 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
                     typename B::Vec xv, av;
                     T::load_coh(sx, i, xv);
                     T::load_coh(sAp, i, av);
-                    B::axpy(xv, alpha, pv);
-                    B::axpy(rv, -alpha, av);
+#pragma unroll
+                    for (int k = 0; k < 6; k++) {
+                        xv.v[k] = fmaf(af, pv.v[k], xv.v[k]);
+                        rv.v[k] = fmaf(-af, av.v[k], rv.v[k]);
+                    }
                     B::store(sx, i, xv);
                     B::store(sr, i, rv);
                 }
                 if (do_p) {
-                    B::xpay(pv, rv, beta);
+#pragma unroll
+                    for (int k = 0; k < 6; k++) pv.v[k] = fmaf(bf, pv.v[k], rv.v[k]);
                     B::store(sp, i, pv);
                     B::store(a.p, s, pv);
                 }
@@ -334,7 +341,7 @@ __global__ void __launch_bounds__(NT, 1) k_cg_phase(const PhaseArgs a)
 inline uint32_t phase_chunk(uint32_t Vh, int sms)
 {
     const uint32_t c = ((Vh + (uint32_t)sms - 1) / (uint32_t)sms + 31u) & ~31u;
-    return (size_t)c * kPhaseSmemPerSite + 4 * sizeof(double) * (size_t)sms <= (size_t)kPhaseMaxSmem ? c : 0u;
+    return (size_t)c * kPhaseSmemPerSite + 4 * sizeof(FF) * (size_t)sms <= (size_t)kPhaseMaxSmem ? c : 0u;
 }
 
 // one block per SM; every block polls every record, so blocks <= NT
@@ -344,7 +351,7 @@ static cudaError_t launch_phase_t(const PhaseArgs &a0, int sms, cudaStream_t st)
     PhaseArgs a = a0;
     a.chunk = phase_chunk(a.Vh, sms);
     if (a.chunk == 0 || sms > NT || sms > kPhaseMaxBlocks) return cudaErrorInvalidConfiguration;
-    const size_t smem = (size_t)a.chunk * kPhaseSmemPerSite + 4 * sizeof(double) * (size_t)sms;
+    const size_t smem = (size_t)a.chunk * kPhaseSmemPerSite + 4 * sizeof(FF) * (size_t)sms;
     // a per-device attribute of the function: set for the current device at every launch
     cudaError_t e0 = cudaFuncSetAttribute(k_cg_phase<PL, NREAL, NT, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           kPhaseMaxSmem);

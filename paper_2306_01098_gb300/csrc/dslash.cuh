@@ -25,6 +25,8 @@ struct DslashArgs {
     const char *pv;
     const char *rv;
     double m4;
+    float m4f;             // m4 and the scales as floats: the persistent CG kernel's FP32 path
+    float scale_f[2];
     const double *shift;   // optional per right-hand side addition to m4 (device)
     Reduce red;
     int zt;                // launch order with z and t interchanged (Geom::zt_ok required)

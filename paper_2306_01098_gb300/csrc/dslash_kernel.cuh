@@ -124,14 +124,18 @@ __device__ __forceinline__ void vec_load(const char *base, uint32_t s, typename 
 template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool COH = false, bool PF = false, int RG = 1,
           class DT = double>
 __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, const char *links, size_t slot_bytes,
-                                            double sc0, double sc1, const char *in, char *outp, const char *pvp,
+                                            std::conditional_t<std::is_same<DT, FF>::value, float, double> sc0,
+                                            std::conditional_t<std::is_same<DT, FF>::value, float, double> sc1,
+                                            const char *in, char *outp, const char *pvp,
                                             const char *rvp, const double *m4r, uint32_t tile,
                                             DT (&dots)[NR * EpiDots<EPI>::n], uint32_t tid = threadIdx.x,
                                             uint32_t ebase = 0)
 {
     static_assert(RG == 1 || DS == 1, "right-hand side groups share a site only with one thread per direction set");
     constexpr int ND = EpiDots<EPI>::n;
-    constexpr bool FFD = std::is_same<DT, FF>::value; // float-float sums (FP32 vectors only)
+    // DT = FF (FP32 vectors inside the persistent CG kernel): float-float dot sums, float
+    // scales (sc0, sc1) and the float m4f, so that no FP64 conversion runs per site
+    constexpr bool FFD = std::is_same<DT, FF>::value;
     static_assert(!FFD || std::is_same<typename Prec<PV>::Vec, FloatArith::Vec>::value,
                   "float-float dot sums are for FP32 iteration vectors");
     using T = Prec<PV>;  // vectors and arithmetic
@@ -266,9 +270,13 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
             if constexpr (EPI >= 1) {
                 typename T::Vec pv;
                 vec_load<T, COH>(pvp + (size_t)r * a.rhs_bytes, s - ebase, pv);
-                T::mdagm_epilogue(out[r], a.m4 + (m4r ? m4r[r] : 0.0), pv);
-                if constexpr (FFD) ff_add(dots[r * ND], T::dotf(pv, out[r]));
-                else dots[r * ND] += T::dot(pv, out[r]);
+                if constexpr (FFD) {
+                    T::mdagm_epilogue(out[r], a.m4f, pv);
+                    ff_add(dots[r * ND], T::dotf(pv, out[r]));
+                } else {
+                    T::mdagm_epilogue(out[r], a.m4 + (m4r ? m4r[r] : 0.0), pv);
+                    dots[r * ND] += T::dot(pv, out[r]);
+                }
                 if constexpr (EPI == 2) {
                     typename T::Vec rv;
                     vec_load<T, COH>(rvp + (size_t)r * a.rhs_bytes, s - ebase, rv);
