@@ -228,6 +228,7 @@ def traffic_for(kernel_key: str):
 def workload_configs(hbm):
     """The other workloads of the benchmark definition, measured after the timed region (one
     GPU, rank 0); every solve to a true FP64 residual <= 1e-10.  Returns a dict for the line.
+      (every solve timed after one untimed call of the same solve)
       64^3x16 (eps 0.3, m 0.01): FP32 Dslash at nrhs 1/4/8/16 (HBM-streaming, L2 flushed),
         mixed CG (FP32 sloppy, FP64 reliable updates) at nrhs 1 and 8 against plain FP64 CG,
         14-shift multi-shift CG (FP32 sloppy), and the 32 uneven lattices batched vs one by one;
@@ -259,7 +260,9 @@ def workload_configs(hbm):
     torch.cuda.empty_cache()
     b1 = fields.gaussian_source(w.dims, w.source_seed, 1, device="cuda")
     x1 = torch.zeros_like(b1)
-    ms64, (rc, st) = timed(lambda: ctx.cg(w.mass, b1, x1.zero_(), tol=w.tol, prec_sloppy=hisq.F64))
+    fp64 = lambda: ctx.cg(w.mass, b1, x1.zero_(), tol=w.tol, prec_sloppy=hisq.F64)
+    fp64()  # untimed: autotuning and first launches
+    ms64, (rc, st) = timed(fp64)
     c["fp64_cg"] = {"nrhs": 1, "ms": ms64, "iterations": st.iterations, "true_residual": st.true_residual}
     c["mixed_cg_f32"] = []
     for nrhs in (1, 8):
@@ -277,9 +280,13 @@ def workload_configs(hbm):
     sig = list(w.shifts)
     xs = [torch.zeros_like(b1[0]) for _ in sig]
     res = torch.zeros(len(sig), dtype=torch.float64)
-    ms, (rc, st) = timed(lambda: ctx.multishift_cg(w.mass, sig, b1[0].contiguous(), xs, tol=[w.tol] * len(sig),
-                                                   prec_sloppy=hisq.F32, prec_precise=hisq.F64, reliable_delta=0.01,
-                                                   residuals=res))
+    def ms14():
+        for t in xs:
+            t.zero_()
+        return ctx.multishift_cg(w.mass, sig, b1[0].contiguous(), xs, tol=[w.tol] * len(sig), prec_sloppy=hisq.F32,
+                                 prec_precise=hisq.F64, reliable_delta=0.01, residuals=res)
+    ms14()  # untimed: autotuning of the 14 right-hand-side finish and first launches
+    ms, (rc, st) = timed(ms14)
     c["multishift_14_f32"] = {"ms": ms, "iterations": st.iterations, "max_true_residual": float(res.max()),
                               "converged": rc == hisq.OK}
     ctx.close()

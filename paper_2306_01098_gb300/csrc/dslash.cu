@@ -112,47 +112,62 @@ DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in
         return best;
     }
     DslashArgs a = make_dslash_args(ctx, pl, 0, in, out, nrhs, rhs_bytes);
+    // ms per launch: one untimed launch (module load, first touch), then one timed launch;
+    // a launch of a millisecond or more is timed well enough by itself, shorter ones take the
+    // best of two rounds of three
     auto time_shape = [&](const DslashShape &sh) -> float {
         if (dslash_launch(pl, pv, 0, a, nreal, sh, st) != cudaSuccess) {
             cudaGetLastError();
             return 1e30f;
         }
-        float best_round = 1e30f;
-        for (int round = 0; round < 2; round++) {
+        float best_launch = 1e30f;
+        for (int round = 0; round < 3; round++) {
+            const int n = round == 0 ? 1 : 3;
             cudaEventRecord(e0, st);
-            for (int i = 0; i < 3; i++) dslash_launch(pl, pv, 0, a, nreal, sh, st);
+            for (int i = 0; i < n; i++) dslash_launch(pl, pv, 0, a, nreal, sh, st);
             cudaEventRecord(e1, st);
             float ms = 0.f;
             if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
                 cudaGetLastError();
                 return 1e30f;
             }
-            best_round = std::min(best_round, ms);
+            best_launch = std::min(best_launch, ms / n);
+            if (round == 0 && ms >= 1.0f) break;
         }
-        return best_round;
+        return best_launch;
+    };
+    auto same = [](const DslashShape &x, const DslashShape &y) {
+        return x.nr == y.nr && x.ds == y.ds && x.order == y.order && x.bs == y.bs && x.rg == y.rg;
+    };
+    auto consider = [&](const DslashShape &sh, float &best_ms) {
+        const float ms = time_shape(sh);
+        if (ms < 0.97f * best_ms) {
+            best_ms = ms;
+            best = sh;
+        }
     };
     const DslashShape def = best;
     float best_ms = time_shape(def);
-    const int bs_max = ctx->batch ? kDslashBlock : kDslashMaxBlock;
+    // stage 1: site order, right-hand sides per thread, threads per site and right-hand-side
+    // groups at the default block size; stage 2: the other block sizes for the winner
     for (int order = 0; order <= (ctx->g.zt_ok ? 1 : 0); order++)
         for (int nr = 1; nr <= cap; nr <<= 1) {
             if (nrhs % nr) continue;
             for (int ds = 1; ds <= 4; ds <<= 1)
                 for (int rg = 1; rg <= (ds == 1 && !ctx->batch && nr <= 4 ? 4 : 1); rg <<= 1) {
                     if (nrhs % (nr * rg)) continue;
-                    for (int bs = ctx->batch ? kDslashBlock : 64; bs <= bs_max; bs <<= 1) {
-                        DslashShape sh{nr, ds, order, bs, rg};
-                        if (sh.nr == def.nr && sh.ds == def.ds && sh.order == def.order && sh.bs == def.bs &&
-                            sh.rg == def.rg)
-                            continue;
-                        const float ms = time_shape(sh);
-                        if (ms < 0.97f * best_ms) {
-                            best_ms = ms;
-                            best = sh;
-                        }
-                    }
+                    const DslashShape sh{nr, ds, order, def.bs, rg};
+                    if (!same(sh, def)) consider(sh, best_ms);
                 }
         }
+    if (!ctx->batch) {
+        const DslashShape stage1 = best;
+        for (int bs = 64; bs <= kDslashMaxBlock; bs <<= 1) {
+            DslashShape sh = stage1;
+            sh.bs = bs;
+            if (!same(sh, stage1)) consider(sh, best_ms);
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->tune[key] = best;

@@ -82,8 +82,8 @@ def run(pairs=2000, epochs=4, test=20, batch=8, lr=2e-3, channels=8, loss=1):
         torch.cuda.synchronize()
         return rc, st, 1e3 * (time.perf_counter() - t)
 
-    for i in range(test):
-        bi = Bt[i].contiguous()
+    for i in range(-1, test):  # source 0 twice: the first pass is untimed (autotuning, first launches)
+        bi = Bt[max(i, 0)].contiguous()
         x = torch.zeros_like(bi)
         for key, fn in (
             ("cg_f64", lambda: ctx.cg(w.mass, bi, x.zero_(), tol=w.tol, prec_sloppy=hisq.F64)),
@@ -94,7 +94,8 @@ def run(pairs=2000, epochs=4, test=20, batch=8, lr=2e-3, channels=8, loss=1):
             ("fcg_net_fp64", lambda: hisq.fcg(ctx, w.mass, bi, x.zero_(), net=net, tol=w.tol, prec_precise=hisq.F64)),
         ):
             rc, st, ms = timed(fn)
-            rows[key].append((rc, st.iterations, st.true_residual, ms))
+            if i >= 0:
+                rows[key].append((rc, st.iterations, st.true_residual, ms))
     for key, v in rows.items():
         out.append({"solve": key, "test_sources": test, "all_converged": all(r[0] == 0 for r in v),
                     "mean_iterations": float(np.mean([r[1] for r in v])),

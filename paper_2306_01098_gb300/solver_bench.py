@@ -28,9 +28,11 @@ if ROOT not in sys.path:
 
 
 def _timed(fn, reps=1):
+    """Best of reps wall times of fn() after one untimed call (which also runs the launch-shape
+    autotuner for any new precision and right-hand-side count)."""
     import torch
     ts = []
-    out = None
+    out = fn()
     for _ in range(reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -114,7 +116,8 @@ def large(reps=1):
 def uneven(reps=3):
     """32 uneven lattices (8^3x8 ... 24^3x8, eps 0.3, m 0.1, 1 source each, FP32 sloppy
     with FP64 reliable updates): one batched Dslash launch against 32 launches, and the
-    batched CG (one graph, all members per launch) against 32 solves one after another."""
+    batched CG (one graph, all members per launch) against 32 solves one after another, both
+    with the multi-kernel iteration and with the persistent phase kernel of a lone solve."""
     import torch
 
     from hisq_inputs import fields, workloads
@@ -151,18 +154,20 @@ def uneven(reps=3):
                  "max_true_residual": float(res.max()), "rc": rc})
     xs = [torch.zeros_like(b) for b in bs]
 
-    def each():
+    def each(persistent):
         worst, its = 0.0, 0
         for c, b, xk in zip(ctxs, bs, xs):
             r1 = torch.zeros(1, dtype=torch.float64)
-            rc1, st1 = c.cg(0.1, b, xk.zero_(), residuals=r1, **kw)
+            rc1, st1 = c.cg(0.1, b, xk.zero_(), residuals=r1, persistent=persistent, **kw)
             worst, its = max(worst, float(r1[0])), max(its, st1.iterations)
         return worst, its
 
-    each()
-    ms1, (worst, its) = _timed(each, reps)
-    rows.append({"solve": "cg", "mode": "per_lattice", "ms": ms1, "max_iterations": its, "max_true_residual": worst,
-                 "speedup_batched": ms1 / ms})
+    # one by one with the same multi-kernel iteration as the batch (the batching gain), and
+    # with each solve's default, the persistent kernel (one cooperative launch per phase)
+    for mode, persistent in (("per_lattice", 0), ("per_lattice_persistent", -1)):
+        ms1, (worst, its) = _timed(lambda: each(persistent), reps)
+        rows.append({"solve": "cg", "mode": mode, "ms": ms1, "max_iterations": its, "max_true_residual": worst,
+                     "speedup_batched": ms1 / ms})
     batch.close()
     for c in ctxs:
         c.close()
