@@ -127,6 +127,7 @@ int hisq_batch_create(hisq_batch **out, int n, hisq_ctx *const *ctxs)
         off[k] = b->total;
         vh[k] = c.g.Vh;
         b->total += c.g.Vh;
+        h->vh[k] = c.g.Vh;
         v->autotune &= c.autotune;
         BatchLattice &L = h->lat[k];
         L.g = c.g;
@@ -135,6 +136,8 @@ int hisq_batch_create(hisq_batch **out, int n, hisq_ctx *const *ctxs)
             L.slot_bytes[p] = c.links[p].slot_bytes;
             L.scale[p][0] = c.links[p].scale[0];
             L.scale[p][1] = c.links[p].scale[1];
+            L.scale_f[p][0] = (float)c.links[p].scale[0];
+            L.scale_f[p][1] = (float)c.links[p].scale[1];
         }
     }
     for (int d = 0; d < 3; d++) {

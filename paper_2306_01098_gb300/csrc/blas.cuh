@@ -20,6 +20,16 @@ struct VecRef {
     __device__ __forceinline__ char *rhs(int r) const { return p + (size_t)r * rb; }
 };
 
+// Sites of each right-hand side: Vh for all of them, or, for a batch of lattices padded to
+// its largest member (per != nullptr, device memory), right-hand side r's own half volume
+// per[r], so that the vector passes never touch the padding.
+struct Len {
+    uint32_t Vh;
+    const uint32_t *per;
+    __host__ __device__ Len(uint32_t vh, const uint32_t *p = nullptr) : Vh(vh), per(p) {}
+    __device__ __forceinline__ uint32_t n(int rhs) const { return per ? per[rhs] : Vh; }
+};
+
 // ---------------------------------------------------------------- element operations
 // y += a x ; y = x + b y ; |x|^2 ; conversions via double components
 template <int P> struct Blas {
@@ -136,11 +146,41 @@ __device__ __forceinline__ void vload(const char *base, uint32_t s, typename Pre
 // ---------------------------------------------------------------- kernels
 // r -= alpha Ap ; |r|^2 reduced with FIN_RR (beta, convergence flags)
 template <int PS>
-__global__ void __launch_bounds__(kVecBlock) k_update_r(VecRef r, VecRef Ap, uint32_t Vh, Reduce red)
+__global__ void __launch_bounds__(kVecBlock) k_update_r(VecRef r, VecRef Ap, Len len, Reduce red)
 {
+    const uint32_t Vh = len.n(blockIdx.y);
     using B = Blas<PS>;
     const int rhs = blockIdx.y;
     const double alpha = alpha_fresh_for_r(red.sc[rhs]) ? red.sc[rhs].alpha : 0.0;
+    if constexpr (std::is_same<typename B::Vec, FloatArith::Vec>::value) {
+        // FP32 records: the update and |r|^2 on the FP32 pipes, summed in float-float pairs
+        // (per thread and per block), one FP64 conversion per block; this GPU issues FP64
+        // operations at 1/64 of the FP32 rate, and an FP64 block sum in every thread of a
+        // multi-right-hand-side grid costs more than the vector traffic
+        FF acc[1] = {{0.f, 0.f}};
+        if (alpha != 0.0) {
+            const float af = (float)alpha;
+            char *rp = r.rhs(rhs);
+            const char *ap = Ap.rhs(rhs);
+            for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+                typename B::Vec rv, av;
+                vload<PS>(rp, s, rv);
+                vload<PS>(ap, s, av);
+                float n2 = 0.f;
+#pragma unroll
+                for (int i = 0; i < 6; i++) {
+                    rv.v[i] = fmaf(-af, av.v[i], rv.v[i]);
+                    n2 = fmaf(rv.v[i], rv.v[i], n2);
+                }
+                B::store(rp, s, rv);
+                ff_add(acc[0], n2);
+            }
+        }
+        block_sum_ff<1>(acc);
+        double mine[1] = {threadIdx.x == 0 ? ff_value(acc[0]) : 0.0};
+        grid_reduce<1>(red, mine, 1, rhs, gridDim.y, blockIdx.x);
+        return;
+    }
     double acc = 0.0;
     if (alpha != 0.0) {
         char *rp = r.rhs(rhs);
@@ -160,9 +200,10 @@ __global__ void __launch_bounds__(kVecBlock) k_update_r(VecRef r, VecRef Ap, uin
 
 // mode 0: x += alpha p, p = r + beta p;  mode 1: x += alpha p;  mode 2: p = r + beta p
 template <int PS, int PX>
-__global__ void __launch_bounds__(kVecBlock) k_update_xp(VecRef x, VecRef p, VecRef r, uint32_t Vh, const Scalars *sc,
+__global__ void __launch_bounds__(kVecBlock) k_update_xp(VecRef x, VecRef p, VecRef r, Len len, const Scalars *sc,
                                                          int mode, const LoopCtl *ctl)
 {
+    const uint32_t Vh = len.n(blockIdx.y);
     if (ctl) mode = ctl->mode; // inside a device-controlled loop
     using BS = Blas<PS>;
     using BX = Blas<PX>;
@@ -197,9 +238,10 @@ __global__ void __launch_bounds__(kVecBlock) k_update_xp(VecRef x, VecRef p, Vec
 //   x += alpha p ; r -= alpha Ap ; p = r + beta p   (p only in mode 0 and while active)
 // alpha is used only if it was produced by this iteration (astamp == it_all - 1).
 template <int PS, int PX>
-__global__ void __launch_bounds__(kVecBlock) k_update_xrp(VecRef x, VecRef p, VecRef r, VecRef Ap, uint32_t Vh,
+__global__ void __launch_bounds__(kVecBlock) k_update_xrp(VecRef x, VecRef p, VecRef r, VecRef Ap, Len len,
                                                           const Scalars *sc, int mode, const LoopCtl *ctl)
 {
+    const uint32_t Vh = len.n(blockIdx.y);
     if (ctl) mode = ctl->mode;
     using BS = Blas<PS>;
     using BX = Blas<PX>;
@@ -235,8 +277,9 @@ __global__ void __launch_bounds__(kVecBlock) k_update_xrp(VecRef x, VecRef p, Ve
 
 // out (PB) = in (PA), element-wise through double components
 template <int PA, int PB>
-__global__ void __launch_bounds__(kVecBlock) k_convert(VecRef in, VecRef out, uint32_t Vh)
+__global__ void __launch_bounds__(kVecBlock) k_convert(VecRef in, VecRef out, Len len)
 {
+    const uint32_t Vh = len.n(blockIdx.y);
     const int rhs = blockIdx.y;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
         typename Blas<PA>::Vec a;
@@ -250,8 +293,9 @@ __global__ void __launch_bounds__(kVecBlock) k_convert(VecRef in, VecRef out, ui
 
 // x_hi (F64) += x_lo (PX); x_lo = 0
 template <int PX>
-__global__ void __launch_bounds__(kVecBlock) k_accum_hi(VecRef xhi, VecRef xlo, uint32_t Vh)
+__global__ void __launch_bounds__(kVecBlock) k_accum_hi(VecRef xhi, VecRef xlo, Len len)
 {
+    const uint32_t Vh = len.n(blockIdx.y);
     const int rhs = blockIdx.y;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
         typename Blas<PX>::Vec l, z;
@@ -270,9 +314,10 @@ __global__ void __launch_bounds__(kVecBlock) k_accum_hi(VecRef xhi, VecRef xlo, 
 
 // r (F64) = b (F64) - Ax (PA) [- shift_rhs x (F64)]; |r|^2 reduced (FIN_STORE -> Scalars.last)
 template <int PA>
-__global__ void __launch_bounds__(kVecBlock) k_residual(VecRef b, VecRef Ax, VecRef r, uint32_t Vh, Reduce red,
+__global__ void __launch_bounds__(kVecBlock) k_residual(VecRef b, VecRef Ax, VecRef r, Len len, Reduce red,
                                                         const double *shift = nullptr, VecRef x = VecRef{nullptr, 0})
 {
+    const uint32_t Vh = len.n(blockIdx.y);
     const int rhs = blockIdx.y;
     const double sh = shift ? shift[rhs] : 0.0;
     double acc = 0.0;
@@ -296,9 +341,33 @@ __global__ void __launch_bounds__(kVecBlock) k_residual(VecRef b, VecRef Ax, Vec
 
 // <a, b> = sum conj(a) b per right-hand side (complex), reduced with FIN_CDOT
 template <int PV>
-__global__ void __launch_bounds__(kVecBlock) k_cdot(VecRef a, VecRef b, uint32_t Vh, Reduce red)
+__global__ void __launch_bounds__(kVecBlock) k_cdot(VecRef a, VecRef b, Len len, Reduce red)
 {
+    const uint32_t Vh = len.n(blockIdx.y);
     const int rhs = blockIdx.y;
+    if constexpr (std::is_same<typename Blas<PV>::Vec, FloatArith::Vec>::value) {
+        // FP32 records: the site's products in FP32, float-float sums per thread and per
+        // block, one FP64 conversion per block (FP64 issues at 1/64 of the FP32 rate here)
+        FF d[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+            typename Blas<PV>::Vec av, bv;
+            vload<PV>(a.rhs(rhs), s, av);
+            vload<PV>(b.rhs(rhs), s, bv);
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const float ar = av.v[2 * i], ai = av.v[2 * i + 1], br = bv.v[2 * i], bi = bv.v[2 * i + 1];
+                sr = fmaf(ar, br, fmaf(ai, bi, sr));
+                si = fmaf(ar, bi, fmaf(-ai, br, si));
+            }
+            ff_add(d[0], sr);
+            ff_add(d[1], si);
+        }
+        block_sum_ff<2>(d);
+        double mine[2] = {threadIdx.x == 0 ? ff_value(d[0]) : 0.0, threadIdx.x == 0 ? ff_value(d[1]) : 0.0};
+        grid_reduce<2>(red, mine, 2, 2 * rhs, 2 * gridDim.y, blockIdx.x);
+        return;
+    }
     double re = 0.0, im = 0.0;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
         typename Blas<PV>::Vec av, bv;
@@ -319,14 +388,40 @@ __global__ void __launch_bounds__(kVecBlock) k_cdot(VecRef a, VecRef b, uint32_t
 // After a reliable update replaced r: remove from p its component along r, then
 // p = r + beta p, i.e. p = (1 - beta <r,p>/|r|^2) r + beta p  (complex coefficient)
 template <int PV>
-__global__ void __launch_bounds__(kVecBlock) k_p_reortho(VecRef p, VecRef r, uint32_t Vh, const Scalars *sc)
+__global__ void __launch_bounds__(kVecBlock) k_p_reortho(VecRef p, VecRef r, Len len, const Scalars *sc)
 {
+    const uint32_t Vh = len.n(blockIdx.y);
     const int rhs = blockIdx.y;
     const Scalars &S = sc[rhs];
     if (!S.active) return;
-    const double beta = S.beta, rr = S.rr;
-    const double cre = rr > 0.0 ? 1.0 - beta * S.last / rr : 1.0;
-    const double cim = rr > 0.0 ? -beta * S.last_im / rr : 0.0;
+    // the coefficients once per block (FP64 divisions in every thread of a large grid cost
+    // more than the pass itself on this GPU's FP64 pipe)
+    __shared__ double coef[3];
+    if (threadIdx.x == 0) {
+        const double beta = S.beta, rr = S.rr;
+        coef[0] = rr > 0.0 ? 1.0 - beta * S.last / rr : 1.0;
+        coef[1] = rr > 0.0 ? -beta * S.last_im / rr : 0.0;
+        coef[2] = beta;
+    }
+    __syncthreads();
+    const double cre = coef[0], cim = coef[1], beta = coef[2];
+    if constexpr (std::is_same<typename Blas<PV>::Vec, FloatArith::Vec>::value) {
+        // FP32 records: the coefficients converted once, the update in FP32
+        const float cf = (float)cre, sf = (float)cim, bf = (float)beta;
+        for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
+            typename Blas<PV>::Vec pv, rv, out;
+            vload<PV>(p.rhs(rhs), s, pv);
+            vload<PV>(r.rhs(rhs), s, rv);
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const float xr = rv.v[2 * i], xi = rv.v[2 * i + 1], yr = pv.v[2 * i], yi = pv.v[2 * i + 1];
+                out.v[2 * i] = fmaf(cf, xr, fmaf(-sf, xi, bf * yr));
+                out.v[2 * i + 1] = fmaf(cf, xi, fmaf(sf, xr, bf * yi));
+            }
+            Blas<PV>::store(p.rhs(rhs), s, out);
+        }
+        return;
+    }
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
         typename Blas<PV>::Vec pv, rv, out;
         vload<PV>(p.rhs(rhs), s, pv);
@@ -343,8 +438,9 @@ __global__ void __launch_bounds__(kVecBlock) k_p_reortho(VecRef p, VecRef r, uin
 }
 
 // |x|^2 (F64) reduced with FIN_STORE
-static __global__ void __launch_bounds__(kVecBlock) k_norm_f64(VecRef x, uint32_t Vh, Reduce red)
+static __global__ void __launch_bounds__(kVecBlock) k_norm_f64(VecRef x, Len len, Reduce red)
 {
+    const uint32_t Vh = len.n(blockIdx.y);
     const int rhs = blockIdx.y;
     double acc = 0.0;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {

@@ -14,6 +14,7 @@
 // triggered every `reliable_interval` iterations, when the sloppy residual fell below
 // delta times the last true one, or when it reached the target.  The solve ends when
 // every recomputed residual |b - A x| / |b| <= tol.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -96,34 +97,34 @@ struct Typed {
         Reduce R = w.red(FIN_RR, w.nblk_vec);
         R.ctl = ctl;
         R.cond = cond;
-        k_update_r<PS><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.r, w.rbS}, VecRef{w.Ap, w.rbS}, w.Vh, R);
+        k_update_r<PS><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.r, w.rbS}, VecRef{w.Ap, w.rbS}, w.len(), R);
     }
     static void update_xrp(SolverWork &w, cudaStream_t st, const LoopCtl *ctl)
     {
         k_update_xrp<PS, PX><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(
-            VecRef{w.xlo, w.rbX}, VecRef{w.p, w.rbS}, VecRef{w.r, w.rbS}, VecRef{w.Ap, w.rbS}, w.Vh, w.sc, 0, ctl);
+            VecRef{w.xlo, w.rbX}, VecRef{w.p, w.rbS}, VecRef{w.r, w.rbS}, VecRef{w.Ap, w.rbS}, w.len(), w.sc, 0, ctl);
     }
     static void update_xp(SolverWork &w, int mode, cudaStream_t st, const LoopCtl *ctl = nullptr)
     {
         k_update_xp<PS, PX><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(
-            VecRef{w.xlo, w.rbX}, VecRef{w.p, w.rbS}, VecRef{w.r, w.rbS}, w.Vh, w.sc, mode, ctl);
+            VecRef{w.xlo, w.rbX}, VecRef{w.p, w.rbS}, VecRef{w.r, w.rbS}, w.len(), w.sc, mode, ctl);
     }
     static void accum_hi(SolverWork &w, cudaStream_t st)
     {
-        k_accum_hi<PX><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.x64, w.rb64}, VecRef{w.xlo, w.rbX}, w.Vh);
+        k_accum_hi<PX><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.x64, w.rb64}, VecRef{w.xlo, w.rbX}, w.len());
     }
     // re-orthogonalise p against the replaced residual, then p = r + beta p
     static void reortho(SolverWork &w, cudaStream_t st)
     {
         const dim3 g(w.nblk_vec, w.nrhs);
-        k_cdot<PS><<<g, kVecBlock, 0, st>>>(VecRef{w.r, w.rbS}, VecRef{w.p, w.rbS}, w.Vh,
+        k_cdot<PS><<<g, kVecBlock, 0, st>>>(VecRef{w.r, w.rbS}, VecRef{w.p, w.rbS}, w.len(),
                                             w.red(FIN_CDOT, w.nblk_vec, w.nblk_vec * w.nrhs));
-        k_p_reortho<PS><<<g, kVecBlock, 0, st>>>(VecRef{w.p, w.rbS}, VecRef{w.r, w.rbS}, w.Vh, w.sc);
+        k_p_reortho<PS><<<g, kVecBlock, 0, st>>>(VecRef{w.p, w.rbS}, VecRef{w.r, w.rbS}, w.len(), w.sc);
     }
     static void from_hi(SolverWork &w, char *dst, cudaStream_t st)
     {
         k_convert<HISQ_F64, PS><<<dim3(w.nblk_vec, w.nrhs), kVecBlock, 0, st>>>(VecRef{w.rhi, w.rb64}, VecRef{dst, w.rbS},
-                                                                               w.Vh);
+                                                                               w.len());
     }
 };
 
@@ -206,11 +207,19 @@ int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out)
     W.px = accum_prec(W.pv);
     W.pp = pp;
     W.Vh = ctx->g.Vh;
+    if (ctx->batch)
+        W.vh_rhs = reinterpret_cast<const uint32_t *>(reinterpret_cast<const char *>(ctx->batch) + offsetof(BatchDesc, vh));
     W.rbS = (size_t)ctx->g.VhPad * spinor_bytes(W.pv);
     W.rbX = (size_t)ctx->g.VhPad * spinor_bytes(W.px);
     W.rb64 = (size_t)ctx->g.Vh * 48;
     W.rbP = (size_t)ctx->g.VhPad * 48;
-    W.nblk_vec = (int)std::min<long>((W.Vh + kVecBlock - 1) / kVecBlock, 4L * ctx->sm_count);
+    // blocks per right-hand side of the vector passes: at most one block per 256 sites and
+    // about one resident wave (eight 256-thread blocks per SM) over all right-hand sides; a
+    // block costs a few memory round trips (scalars, arrival) whatever its share of sites,
+    // so with many right-hand sides (a batch of small lattices) extra waves of nearly empty
+    // blocks took longer than the vector traffic
+    W.nblk_vec = (int)std::min<long>({(W.Vh + kVecBlock - 1) / kVecBlock, 4L * ctx->sm_count,
+                                      std::max(1L, 8L * ctx->sm_count / nrhs)});
     W.nblk_dslash = (int)((4ull * W.Vh + 63) / 64); // blocks at 4 threads per site and 64 threads per block (upper bound)
     int rc = HISQ_OK;
     auto A = [&](char **p, size_t b) { if (rc == HISQ_OK) rc = W.alloc(ctx, p, b); };
@@ -515,13 +524,13 @@ int precise_residual(hisq_ctx *ctx, SolverWork &w, double m, cudaStream_t st, in
     if (prec == HISQ_F64) {
         if ((rc = apply_mdagm(ctx, HISQ_F64, m, w.x64, w.thi, w.Axhi, w.nrhs, w.rb64, st, nullptr, true))) return rc;
         k_residual<HISQ_F64><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axhi, w.rb64}, VecRef{w.rhi, w.rb64},
-                                                     w.Vh, w.red(FIN_STORE, w.nblk_vec), w.shift,
+                                                     w.len(), w.red(FIN_STORE, w.nblk_vec), w.shift,
                                                      VecRef{w.x64, w.rb64});
     } else {
-        k_convert<HISQ_F64, HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.x64, w.rb64}, VecRef{w.xx, w.rbP}, w.Vh);
+        k_convert<HISQ_F64, HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.x64, w.rb64}, VecRef{w.xx, w.rbP}, w.len());
         if ((rc = apply_mdagm(ctx, HISQ_F64X, m, w.xx, w.tx, w.Axx, w.nrhs, w.rbP, st, nullptr, true))) return rc;
         k_residual<HISQ_F64X><<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, VecRef{w.Axx, w.rbP}, VecRef{w.rhi, w.rb64},
-                                                      w.Vh, w.red(FIN_STORE, w.nblk_vec), w.shift,
+                                                      w.len(), w.red(FIN_STORE, w.nblk_vec), w.shift,
                                                       VecRef{w.x64, w.rb64});
     }
     HISQ_CUDA(ctx, cudaGetLastError());
@@ -573,12 +582,12 @@ int run_cg(hisq_ctx *ctx, double m, const double *b, double *x, int nrhs, const 
     const double tol2 = o.tol * o.tol;
     const double delta2 = o.reliable_delta * o.reliable_delta;
     // |b|^2
-    k_norm_f64<<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, w.Vh, w.red(FIN_STORE, w.nblk_vec));
+    k_norm_f64<<<g, kVecBlock, 0, st>>>(VecRef{w.b64, w.rb64}, w.len(), w.red(FIN_STORE, w.nblk_vec));
     k_scalars<<<1, 64, 0, st>>>(w.sc, nrhs, SC_INIT_BB, tol2, ps == HISQ_F64 ? 0.0 : delta2);
     // r_hi = b - A x0
     if (o.zero_guess) {
         HISQ_CUDA(ctx, cudaMemcpyAsync(w.rhi, w.b64, vb, cudaMemcpyDeviceToDevice, st));
-        k_norm_f64<<<g, kVecBlock, 0, st>>>(VecRef{w.rhi, w.rb64}, w.Vh, w.red(FIN_STORE, w.nblk_vec));
+        k_norm_f64<<<g, kVecBlock, 0, st>>>(VecRef{w.rhi, w.rb64}, w.len(), w.red(FIN_STORE, w.nblk_vec));
     } else if ((rc = precise_residual(ctx, w, m, st, w.pp))) {
         return rc;
     }

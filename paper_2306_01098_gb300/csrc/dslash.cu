@@ -24,6 +24,10 @@ cudaError_t dslash_launch(int pl, int pv, int epi, const DslashArgs &a, int nrea
     DslashArgs b = a;
     b.zt = sh.order;
     b.bs = sh.bs;
+    // float copies for the FP32-vector kernels
+    b.m4f = (float)b.m4;
+    b.scale_f[0] = (float)b.scale[0];
+    b.scale_f[1] = (float)b.scale[1];
     if (pl == pv) {
         switch (pl) {
         case HISQ_F64: return dslash_launch_HISQ_F64_HISQ_F64(epi, b, nreal, nr, ds, sh.rg, st);

@@ -271,7 +271,7 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
                 typename T::Vec pv;
                 vec_load<T, COH>(pvp + (size_t)r * a.rhs_bytes, s - ebase, pv);
                 if constexpr (FFD) {
-                    T::mdagm_epilogue(out[r], a.m4f, pv);
+                    T::mdagm_epilogue(out[r], m4r ? a.m4f + (float)m4r[r] : a.m4f, pv);
                     ff_add(dots[r * ND], T::dotf(pv, out[r]));
                 } else {
                     T::mdagm_epilogue(out[r], a.m4 + (m4r ? m4r[r] : 0.0), pv);
@@ -295,6 +295,16 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
         }
     }
 }
+
+// block sums of the epilogue's dot products (valid on thread 0): float-float or FP64
+template <bool FFK, int N, class D>
+__device__ __forceinline__ void block_sum_dots(D (&d)[N])
+{
+    if constexpr (FFK) block_sum_ff<N>(d);
+    else block_sum_multi<N>(d);
+}
+__device__ __forceinline__ double dot_value(const FF &x) { return ff_value(x); }
+__device__ __forceinline__ double dot_value(double x) { return x; }
 
 // BATCH: the lattices of a batch in one launch (NR = 1; right-hand side k is lattice k).
 // RG: groups of right-hand sides sharing a site's threads (dslash_item).
@@ -323,34 +333,58 @@ __global__ void __launch_bounds__(kDslashMaxBlock) k_dslash(const DslashArgs a)
         }
     }
     constexpr int ND = EpiDots<EPI>::n;
-    double dots[NR * ND];
+    // FP32 vectors: the epilogue's dot products in float-float pairs, float scales and m4
+    // (no FP64 operation per site or per thread; one conversion per block and value)
+    constexpr bool FFK = PV == HISQ_F32 && RG == 1;
+    using DTK = std::conditional_t<FFK, FF, double>;
+    DTK dots[NR * ND];
 #pragma unroll
-    for (int r = 0; r < NR * ND; r++) dots[r] = 0.0;
+    for (int r = 0; r < NR * ND; r++) dots[r] = DTK{};
     if constexpr (BATCH) {
+        // One block per tile; with the epilogue's reduction a resident grid whose blocks
+        // stride over the tiles: each tile's dot products go to its own partial (the tile
+        // number of its lattice), and a block arrives once, after its last tile, instead of
+        // every tile paying the block sum's barriers and the arrival's round trip in a wave
+        // of its own.
         __shared__ Geom sg;
         constexpr int d = DS == 1 ? 0 : DS == 2 ? 1 : 2;
         const BatchDesc &B = *a.batch;
-        const uint32_t item = blockIdx.x;
-        int k = 0;
-        while (k + 1 < B.n && B.tstart[d][k + 1] <= item) k++;
-        const uint32_t tile = item - B.tstart[d][k];
-        if (threadIdx.x == 0) sg = B.lat[k].g;
-        __syncthreads();
-        const size_t off = (size_t)k * a.rhs_bytes;
-        dslash_item<PL, PV, NREAL, 1, EPI, DS>(a, sg, B.lat[k].links[PL], B.lat[k].slot_bytes[PL], B.lat[k].scale[PL][0],
-                                               B.lat[k].scale[PL][1], a.in + off, a.out + off,
-                                               EPI ? a.pv + off : nullptr, EPI == 2 ? a.rv + off : nullptr,
-                                               a.shift ? a.shift + k : nullptr, tile, dots);
-        if constexpr (EPI >= 1) {
-            if (a.red.partials) {
-                block_sum_multi<ND>(dots);
-                // partials of lattice k beyond its own tiles are zero
-                if (threadIdx.x == 0 && tile == 0)
-                    for (int j = 0; j < ND; j++)
-                        for (int i = (int)(B.tstart[d][k + 1] - B.tstart[d][k]); i < a.red.nblocks; i++)
-                            a.red.partials[(size_t)(ND * k + j) * a.red.nblocks + i] = 0.0;
-                grid_reduce<ND>(a.red, dots, ND, ND * k, ND * a.nrhs, (int)tile);
+        for (uint32_t item = blockIdx.x; item < a.items; item += gridDim.x) {
+            int k = 0;
+            while (k + 1 < B.n && B.tstart[d][k + 1] <= item) k++;
+            const uint32_t tile = item - B.tstart[d][k];
+            __syncthreads(); // the previous tile's readers of sg are done
+            if (threadIdx.x == 0) sg = B.lat[k].g;
+            __syncthreads();
+            const size_t off = (size_t)k * a.rhs_bytes;
+            const BatchLattice &L = B.lat[k];
+            const auto sc0 = [&] { if constexpr (FFK) return L.scale_f[PL][0]; else return L.scale[PL][0]; }();
+            const auto sc1 = [&] { if constexpr (FFK) return L.scale_f[PL][1]; else return L.scale[PL][1]; }();
+            DTK td[ND];
+#pragma unroll
+            for (int j = 0; j < ND; j++) td[j] = DTK{};
+            dslash_item<PL, PV, NREAL, 1, EPI, DS, false, false, 1, DTK>(
+                a, sg, L.links[PL], L.slot_bytes[PL], sc0, sc1, a.in + off, a.out + off, EPI ? a.pv + off : nullptr,
+                EPI == 2 ? a.rv + off : nullptr, a.shift ? a.shift + k : nullptr, tile, td);
+            if constexpr (EPI >= 1) {
+                if (a.red.partials) {
+                    block_sum_dots<FFK, ND>(td);
+                    if (threadIdx.x == 0) {
+#pragma unroll
+                        for (int j = 0; j < ND; j++)
+                            a.red.partials[(size_t)(ND * k + j) * a.red.nblocks + tile] = dot_value(td[j]);
+                        // partials of lattice k beyond its own tiles are zero
+                        if (tile == 0)
+                            for (int j = 0; j < ND; j++)
+                                for (int i = (int)(B.tstart[d][k + 1] - B.tstart[d][k]); i < a.red.nblocks; i++)
+                                    a.red.partials[(size_t)(ND * k + j) * a.red.nblocks + i] = 0.0;
+                    }
+                }
             }
+        }
+        if constexpr (EPI >= 1) {
+            // the partials are in place: arrive (no values of its own), the last block finishes
+            if (a.red.partials) grid_reduce<ND>(a.red, nullptr, 0, 0, ND * a.nrhs, 0);
         }
     } else {
         // gridDim.x is a multiple of the group count, so a block keeps one group of right-hand
@@ -358,16 +392,20 @@ __global__ void __launch_bounds__(kDslashMaxBlock) k_dslash(const DslashArgs a)
         const uint32_t ngroups = (uint32_t)(a.nrhs / (NR * RG));
         const int rhs0 = (int)(blockIdx.x % ngroups) * NR * RG;
         const size_t off = (size_t)rhs0 * a.rhs_bytes;
+        const auto sc0 = [&] { if constexpr (FFK) return a.scale_f[0]; else return a.scale[0]; }();
+        const auto sc1 = [&] { if constexpr (FFK) return a.scale_f[1]; else return a.scale[1]; }();
         for (uint32_t item = blockIdx.x; item < a.items; item += gridDim.x)
-            dslash_item<PL, PV, NREAL, NR, EPI, DS, false, false, RG>(
-                a, a.g, a.links, a.slot_bytes, a.scale[0], a.scale[1], a.in + off, a.out + off,
-                EPI ? a.pv + off : nullptr, EPI == 2 ? a.rv + off : nullptr, a.shift ? a.shift + rhs0 : nullptr,
-                item / ngroups, dots);
+            dslash_item<PL, PV, NREAL, NR, EPI, DS, false, false, RG, DTK>(
+                a, a.g, a.links, a.slot_bytes, sc0, sc1, a.in + off, a.out + off, EPI ? a.pv + off : nullptr,
+                EPI == 2 ? a.rv + off : nullptr, a.shift ? a.shift + rhs0 : nullptr, item / ngroups, dots);
         if constexpr (EPI >= 1) {
             if (a.red.partials) { // uniform over the grid
                 if constexpr (RG == 1) {
-                    block_sum_multi<NR * ND>(dots);
-                    grid_reduce<NR * ND>(a.red, dots, NR * ND, ND * rhs0, ND * a.nrhs, (int)(blockIdx.x / ngroups));
+                    block_sum_dots<FFK, NR * ND>(dots);
+                    double dd[NR * ND];
+#pragma unroll
+                    for (int j = 0; j < NR * ND; j++) dd[j] = threadIdx.x == 0 ? dot_value(dots[j]) : 0.0; // read on thread 0
+                    grid_reduce<NR * ND>(a.red, dd, NR * ND, ND * rhs0, ND * a.nrhs, (int)(blockIdx.x / ngroups));
                 } else {
                     const double *sums = block_sum_groups<NR * ND, RG>(dots);
                     grid_reduce<NR * ND>(a.red, sums, RG * NR * ND, ND * rhs0, ND * a.nrhs,
@@ -401,13 +439,15 @@ static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
             o = 1;
         occ[bi] = o;
     }
-    if constexpr (BATCH) { // one block per tile of every lattice
+    if constexpr (BATCH) { // one block per tile of every lattice; a resident grid with a reduction
         constexpr int d = DS == 1 ? 0 : DS == 2 ? 1 : 2;
         const uint32_t items = a.batch_tiles[d];
+        const uint32_t resident = (uint32_t)std::max(1, a.sm_count) * (uint32_t)occ[bi];
+        const uint32_t blocks = a.red.partials ? std::min(items, resident) : items;
         a.items = items;
         a.red.nblocks = (int)a.batch_maxtiles[d]; // partials per lattice (zero beyond its tiles)
-        a.red.ntotal = (int)items;
-        k_dslash<PL, PV, NREAL, 1, EPI, DS, true><<<items, kDslashBlock, 0, st>>>(a);
+        a.red.ntotal = (int)blocks;
+        k_dslash<PL, PV, NREAL, 1, EPI, DS, true><<<blocks, kDslashBlock, 0, st>>>(a);
         return cudaGetLastError();
     } else {
         const size_t tiles = ((size_t)a.g.Vh * DS * RG + bs - 1) / bs;

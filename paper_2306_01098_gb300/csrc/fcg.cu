@@ -89,12 +89,14 @@ __device__ __forceinline__ void fcg_reduce(double (&v)[NV], double *partials, un
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; k++) partials[k * nb + blockIdx.x] = v[k];
-        __threadfence();
-        last = atomicAdd(counter, 1u) == (unsigned)nb - 1;
+        // acquire-release arrival (publishes the partials; the last block sees all of them)
+        unsigned prev;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(counter) : "memory");
+        last = prev == (unsigned)nb - 1;
     }
     __syncthreads();
     if (!last) return;
-    __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     double tot[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) {

@@ -211,6 +211,7 @@ struct BatchLattice {
     const char *links[HISQ_NPREC];
     size_t slot_bytes[HISQ_NPREC];
     double scale[HISQ_NPREC][2];
+    float scale_f[HISQ_NPREC][2]; // the same as floats (FP32-vector kernels)
 };
 
 // Device table of a batch.  Work items of one launch are the site tiles of every lattice
@@ -220,6 +221,7 @@ struct BatchDesc {
     int n;
     uint32_t tstart[3][kMaxBatch + 1];
     uint32_t maxtiles[3]; // most tiles of one lattice
+    uint32_t vh[kMaxBatch]; // half volume of each lattice (the sites of its right-hand side)
     BatchLattice lat[kMaxBatch];
 };
 

@@ -320,9 +320,10 @@ __device__ __forceinline__ const double *block_sum_groups(double (&x)[NV])
 
 // Grid reduction of `nval_all` values.  Block (bx, by) supplies the block sums of values
 // [vbase, vbase + nmine) (thread 0 reads them from `mine`, registers or shared memory) as
-// partial number bx of each; NV is how many values the finishing block sums at once;
+// partial number bx of each;
 // the last of the R.ntotal blocks to arrive sums the R.nblocks partials of every value
-// in a fixed order and applies R.op.  The counter is reset for the next use.
+// in a fixed order and applies R.op.  The counter is reset for the next use.  NV is the
+// number of values a call site supplies at once (the tail does not depend on it).
 template <int NV>
 __device__ __forceinline__ void grid_reduce(const Reduce &R, const double *mine, int nmine, int vbase, int nval_all,
                                             int bx)
@@ -330,36 +331,38 @@ __device__ __forceinline__ void grid_reduce(const Reduce &R, const double *mine,
     __shared__ bool last;
     if (threadIdx.x == 0) {
         for (int v = 0; v < nmine; v++) R.partials[(size_t)(vbase + v) * R.nblocks + bx] = mine[v];
-        __threadfence();
-        const unsigned prev = atomicAdd(R.counter, 1u);
+        // the arrival is an acquire-release add: it publishes this block's partials and, in
+        // the last block, makes every other block's visible
+        unsigned prev;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(R.counter) : "memory");
         last = (prev == (unsigned)R.ntotal - 1);
     }
     __syncthreads();
     if (!last) return;
-    __threadfence();
-    // NV values at a time through one block-wide reduction (the same summation order as one
-    // value at a time, fewer barriers in this serial tail); finished in value order
-    for (int v0 = 0; v0 < nval_all; v0 += NV) {
-        double x[NV];
-#pragma unroll
-        for (int k = 0; k < NV; k++) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    // One warp per scalar slot (the four values of FIN_AB, the two of FIN_CDOT, else one
+    // value): the warp's lanes sum the value's partials in a fixed order (lane l takes
+    // partials l, l + 32, ... four at a time, then a fixed shuffle tree) and lane 0 finishes
+    // the slot's values in value order.  Right-hand sides are finished in parallel, so the
+    // serial tail does not grow with their number; the order is the same in every run.
+    const int per = R.op == FIN_AB ? 4 : R.op == FIN_CDOT ? 2 : 1;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    for (int u = w; u < nval_all / per; u += nw)
+        for (int j = 0; j < per; j++) {
+            const int v = u * per + j;
+            const double *pv = R.partials + (size_t)v * R.nblocks;
             double acc = 0.0;
-            if (v0 + k < nval_all) {
-                const double *pv = R.partials + (size_t)(v0 + k) * R.nblocks;
-                for (int i0 = threadIdx.x; i0 < R.nblocks; i0 += 4 * blockDim.x) {
-                    double t[4];
+            for (int i0 = l; i0 < R.nblocks; i0 += 128) {
+                double t[4];
 #pragma unroll
-                    for (int u = 0; u < 4; u++)
-                        t[u] = i0 + u * (int)blockDim.x < R.nblocks ? __ldcg(pv + i0 + u * blockDim.x) : 0.0;
-                    acc += (t[0] + t[1]) + (t[2] + t[3]);
-                }
+                for (int q = 0; q < 4; q++) t[q] = i0 + 32 * q < R.nblocks ? __ldcg(pv + i0 + 32 * q) : 0.0;
+                acc += (t[0] + t[1]) + (t[2] + t[3]);
             }
-            x[k] = acc;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (l == 0) finish_value(R, v, acc);
         }
-        block_sum_multi<NV>(x);
-        if (threadIdx.x == 0)
-            for (int k = 0; k < NV && v0 + k < nval_all; k++) finish_value(R, v0 + k, x[k]);
-    }
+    __syncthreads(); // every slot finished before the loop control reads the flags
     if (threadIdx.x == 0) {
         finish_control(R, R.op == FIN_AB ? nval_all / 4 : R.op == FIN_CDOT ? nval_all / 2 : nval_all);
         __threadfence();

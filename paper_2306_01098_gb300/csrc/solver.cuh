@@ -3,6 +3,7 @@
 
 #include <vector>
 
+#include "blas.cuh"
 #include "reduce.cuh"
 
 namespace hisq {
@@ -12,6 +13,7 @@ struct SolverWork {
     DslashShape shape;
     bool tuned = false;
     uint32_t Vh = 0;
+    const uint32_t *vh_rhs = nullptr; // batches: each right-hand side's own half volume (device)
     size_t rbS = 0, rbX = 0, rb64 = 0, rbP = 0; // bytes per rhs: sloppy, accumulator, canonical F64, padded F64
     char *r = nullptr, *p = nullptr, *Ap = nullptr, *t = nullptr, *xlo = nullptr; // sloppy vectors
     char *b64 = nullptr, *x64 = nullptr, *rhi = nullptr, *Axhi = nullptr, *thi = nullptr; // FP64
@@ -40,6 +42,8 @@ struct SolverWork {
     void release();
     int alloc(hisq_ctx *ctx, char **ptr, size_t bytes);
     Reduce red(int op, int nblocks_per_value, int ntotal = 0) const;
+    // sites the vector passes cover per right-hand side (a batch skips its padding)
+    Len len() const { return Len(Vh, vh_rhs); }
 };
 
 int get_work(hisq_ctx *ctx, int nrhs, int ps, int pp, SolverWork **out);
