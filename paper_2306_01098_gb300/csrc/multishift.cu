@@ -136,24 +136,51 @@ __global__ void __launch_bounds__(kVecBlock) k_shift_update(VecRef x, VecRef p, 
     using BS = Blas<PS>;
     using BX = Blas<PX>;
     static_assert(std::is_same<typename BS::Vec, typename BX::Vec>::value, "accumulator shares the sloppy vector type");
+    // The shifts' coefficients once per block: read from global memory, compared and
+    // converted per site and shift, they kept this GPU's FP64 pipe (1/64 of the FP32 rate)
+    // busy for about four operations per site and shift.  FP32 vectors use float copies.
+    constexpr bool FL = std::is_same<typename BS::Vec, FloatArith::Vec>::value;
+    __shared__ double cd[3][kMaxShift];
+    __shared__ float cf[3][kMaxShift];
+    __shared__ int on[kMaxShift], act[kMaxShift];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        cd[0][k] = ss->alpha_s[k];
+        cd[1][k] = ss->zeta_new[k];
+        cd[2][k] = ss->beta_s[k];
+        for (int i = 0; i < 3; i++) cf[i][k] = (float)cd[i][k];
+        on[k] = cd[0][k] != 0.0;
+        act[k] = ss->active[k];
+    }
+    __syncthreads();
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < Vh; s += gridDim.x * blockDim.x) {
         typename BS::Vec rv;
         bool have_r = false;
         for (int k = 0; k < n; k++) {
-            const double as = ss->alpha_s[k];
-            if (as == 0.0) continue;
+            if (!on[k]) continue;
             typename BS::Vec pv;
             vload<PS>(p.rhs(k), s, pv);
             typename BX::Vec xv;
             vload<PX>(x.rhs(k), s, xv);
-            BX::axpy(xv, as, pv);
+            if constexpr (FL) {
+                const float a = cf[0][k];
+#pragma unroll
+                for (int i = 0; i < 6; i++) xv.v[i] = fmaf(a, pv.v[i], xv.v[i]);
+            } else {
+                BX::axpy(xv, cd[0][k], pv);
+            }
             BX::store(x.rhs(k), s, xv);
-            if (ss->active[k]) {
+            if (act[k]) {
                 if (!have_r) {
                     vload<PS>(r.rhs(0), s, rv);
                     have_r = true;
                 }
-                BS::axpby(pv, ss->zeta_new[k], rv, ss->beta_s[k]);
+                if constexpr (FL) {
+                    const float z = cf[1][k], b = cf[2][k];
+#pragma unroll
+                    for (int i = 0; i < 6; i++) pv.v[i] = fmaf(z, rv.v[i], b * pv.v[i]);
+                } else {
+                    BS::axpby(pv, cd[1][k], rv, cd[2][k]);
+                }
                 BS::store(p.rhs(k), s, pv);
             }
         }

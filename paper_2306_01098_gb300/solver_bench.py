@@ -113,11 +113,13 @@ def large(reps=1):
     return rows
 
 
-def uneven(reps=3):
+def uneven(reps=3, batched_only=False, use_graph=1, nvtx=False):
     """32 uneven lattices (8^3x8 ... 24^3x8, eps 0.3, m 0.1, 1 source each, FP32 sloppy
     with FP64 reliable updates): one batched Dslash launch against 32 launches, and the
     batched CG (one graph, all members per launch) against 32 solves one after another, both
-    with the multi-kernel iteration and with the persistent phase kernel of a lone solve."""
+    with the multi-kernel iteration and with the persistent phase kernel of a lone solve.
+    batched_only: the batched solve alone; use_graph = 0: its iterations as direct launches;
+    nvtx: one more batched solve inside an NVTX range "timed" (for ncu --nvtx-include)."""
     import torch
 
     from hisq_inputs import fields, workloads
@@ -148,10 +150,22 @@ def uneven(reps=3):
     kw = dict(tol=1e-10, prec_sloppy=hisq.F32, prec_precise=hisq.F64, reliable_delta=0.01)
     x = torch.zeros_like(bp)
     res = torch.zeros(len(dims), dtype=torch.float64)
-    batch.cg([0.1] * len(dims), bp, x.zero_(), residuals=res, **kw)
-    ms, (rc, st) = _timed(lambda: batch.cg([0.1] * len(dims), bp, x.zero_(), residuals=res, **kw), reps)
-    rows.append({"solve": "cg", "mode": "batched", "ms": ms, "iterations": st.iterations,
+    bkw = dict(kw, use_graph=use_graph)
+    batch.cg([0.1] * len(dims), bp, x.zero_(), residuals=res, **bkw)
+    ms, (rc, st) = _timed(lambda: batch.cg([0.1] * len(dims), bp, x.zero_(), residuals=res, **bkw), reps)
+    rows.append({"solve": "cg", "mode": "batched", "use_graph": use_graph, "ms": ms, "iterations": st.iterations,
                  "max_true_residual": float(res.max()), "rc": rc})
+    if nvtx:
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        batch.cg([0.1] * len(dims), bp, x.zero_(), residuals=res, **bkw)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    if batched_only:
+        batch.close()
+        for c in ctxs:
+            c.close()
+        return rows
     xs = [torch.zeros_like(b) for b in bs]
 
     def each(persistent):
@@ -277,9 +291,15 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", choices=["batched", "large", "uneven", "rational", "smear", "meson"], default="batched")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--batched-only", action="store_true", help="uneven: the batched solve alone")
+    ap.add_argument("--use-graph", type=int, default=1, help="uneven: 0 runs the batched iterations as direct launches")
+    ap.add_argument("--nvtx", action="store_true", help="uneven: one more batched solve in an NVTX range 'timed'")
     a = ap.parse_args()
-    rows = {"batched": batched, "large": large, "uneven": uneven, "rational": rational_workload,
-            "smear": smear_workload, "meson": meson_workload}[a.workload](a.reps)
+    if a.workload == "uneven":
+        rows = uneven(a.reps, a.batched_only, a.use_graph, a.nvtx)
+    else:
+        rows = {"batched": batched, "large": large, "rational": rational_workload,
+                "smear": smear_workload, "meson": meson_workload}[a.workload](a.reps)
     for r in rows:
         print(json.dumps(r), flush=True)
 
