@@ -194,6 +194,17 @@ int hisq_tune_set_groups(hisq_ctx *ctx, int prec_links, int prec_vectors, int nr
 /* The stored shape for the key: shape = {n_inner, threads_per_site, site_order,
  * threads_per_block, rhs_groups}; HISQ_EINVAL if none is stored yet. */
 int hisq_tune_get(const hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int shape[5]);
+/* Groups of right-hand sides per block (1, 2 or 4; the N_outer loop of Sec. 5.1 moved into
+ * the block) of the stored shape: with g > 1 the block's threads form g slices over the same
+ * sites, slice k taking the k-th of the block's g groups of n_inner right-hand sides, and the
+ * links are loaded through L1 so that one read from L2 serves all g groups.  Only the plain
+ * Dslash uses it (a solver's normal-operator launches keep one group per block); requires
+ * threads_per_site 1, n_inner <= 4, rhs_groups 1, at least 32 threads per slice and
+ * g n_inner dividing nrhs, else HISQ_EINVAL (also when no shape is stored).  The autotuner
+ * searches it.  Results do not depend on it. */
+int hisq_tune_set_block_groups(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int block_groups);
+/* The stored shape's groups of right-hand sides per block; HISQ_EINVAL if none is stored. */
+int hisq_tune_get_block_groups(const hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int *block_groups);
 
 /* ------------------------------------------------------------------ solvers */
 typedef struct {

@@ -72,9 +72,37 @@ __device__ __forceinline__ uint32_t ld_nc4(const void *p, uint64_t pol)
     return r;
 }
 
+// the same loads kept in L1 (read-only path, L1 allocation): links that other warps of the
+// same block read again right afterwards (right-hand-side groups sharing a block's sites)
+__device__ __forceinline__ uint4 ld_l1_16(const void *p, uint64_t pol, bool hint)
+{
+    uint4 r;
+    if (hint)
+        asm("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+            : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+            : "l"(p), "l"(pol));
+    else
+        asm("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint2 ld_l1_8(const void *p, uint64_t pol, bool hint)
+{
+    uint2 r;
+    if (hint) asm("ld.global.nc.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;" : "=r"(r.x), "=r"(r.y) : "l"(p), "l"(pol));
+    else asm("ld.global.nc.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_l1_4(const void *p, uint64_t pol, bool hint)
+{
+    uint32_t r;
+    if (hint) asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+    else asm("ld.global.nc.u32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+
 // link words of site s in a slot; LB = link bytes.  With `hint`, the loads are marked
-// evict-first in L2.
-template <int LB>
+// evict-first in L2; with L1, they allocate in L1 (read again by other warps of the block).
+template <int LB, bool L1 = false>
 __device__ __forceinline__ void load_link_words(const char *slot, uint32_t s, uint32_t (&w)[LB / 4], bool hint = false)
 {
     constexpr int NQ = LB / 16, TB = LB % 16;
@@ -84,7 +112,7 @@ __device__ __forceinline__ void load_link_words(const char *slot, uint32_t s, ui
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
         const char *a = blk + q * 512 + lane * 16;
-        uint4 v = hint ? ld_nc16(a, pol) : ld_nc16(a);
+        uint4 v = L1 ? ld_l1_16(a, pol, hint) : hint ? ld_nc16(a, pol) : ld_nc16(a);
         w[4 * q + 0] = v.x;
         w[4 * q + 1] = v.y;
         w[4 * q + 2] = v.z;
@@ -92,12 +120,12 @@ __device__ __forceinline__ void load_link_words(const char *slot, uint32_t s, ui
     }
     if constexpr (TB == 8) {
         const char *a = blk + NQ * 512 + lane * 8;
-        uint2 v = hint ? ld_nc8(a, pol) : ld_nc8(a);
+        uint2 v = L1 ? ld_l1_8(a, pol, hint) : hint ? ld_nc8(a, pol) : ld_nc8(a);
         w[4 * NQ + 0] = v.x;
         w[4 * NQ + 1] = v.y;
     } else if constexpr (TB == 4) {
         const char *a = blk + NQ * 512 + lane * 4;
-        w[4 * NQ] = hint ? ld_nc4(a, pol) : ld_nc4(a);
+        w[4 * NQ] = L1 ? ld_l1_4(a, pol, hint) : hint ? ld_nc4(a, pol) : ld_nc4(a);
     }
 }
 

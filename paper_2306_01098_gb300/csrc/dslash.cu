@@ -24,6 +24,7 @@ cudaError_t dslash_launch(int pl, int pv, int epi, const DslashArgs &a, int nrea
     DslashArgs b = a;
     b.zt = sh.order;
     b.bs = sh.bs;
+    b.wg = epi ? 1 : sh.wg; // the epilogue launches of a solver keep one group per block
     // float copies for the FP32-vector kernels
     b.m4f = (float)b.m4;
     b.scale_f[0] = (float)b.scale[0];
@@ -141,7 +142,7 @@ DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in
         return best_launch;
     };
     auto same = [](const DslashShape &x, const DslashShape &y) {
-        return x.nr == y.nr && x.ds == y.ds && x.order == y.order && x.bs == y.bs && x.rg == y.rg;
+        return x.nr == y.nr && x.ds == y.ds && x.order == y.order && x.bs == y.bs && x.rg == y.rg && x.wg == y.wg;
     };
     auto consider = [&](const DslashShape &sh, float &best_ms) {
         const float ms = time_shape(sh);
@@ -163,6 +164,9 @@ DslashShape dslash_shape(hisq_ctx *ctx, int pl, int pv, int nrhs, const void *in
                     const DslashShape sh{nr, ds, order, def.bs, rg};
                     if (!same(sh, def)) consider(sh, best_ms);
                 }
+            // groups of right-hand sides in one block, links shared through L1
+            for (int wg = 2; wg <= 4 && !ctx->batch && nr <= 4; wg <<= 1)
+                if (nrhs % (nr * wg) == 0) consider(DslashShape{nr, 1, order, def.bs, 1, wg}, best_ms);
         }
     if (!ctx->batch) {
         const DslashShape stage1 = best;
@@ -222,7 +226,7 @@ extern "C" int hisq_tune_set_block(hisq_ctx *ctx, int prec_links, int prec_vecto
     auto it = ctx->tune.find(tune_key(prec_links, prec_vectors, nrhs));
     if (it == ctx->tune.end()) return set_error(ctx, HISQ_EINVAL, "hisq_tune_set_block: no shape for this key");
     if ((threads_per_block != 64 && threads_per_block != 128 && threads_per_block != 256) ||
-        (ctx->batch && threads_per_block != kDslashBlock))
+        (ctx->batch && threads_per_block != kDslashBlock) || threads_per_block / it->second.wg < 32)
         return set_error(ctx, HISQ_EINVAL, "hisq_tune_set_block: threads per block must be 64, 128 or 256");
     it->second.bs = threads_per_block;
     return HISQ_OK;
@@ -235,10 +239,36 @@ extern "C" int hisq_tune_set_groups(hisq_ctx *ctx, int prec_links, int prec_vect
     if (it == ctx->tune.end()) return set_error(ctx, HISQ_EINVAL, "hisq_tune_set_groups: no shape for this key");
     const DslashShape &sh = it->second;
     if ((rhs_groups != 1 && rhs_groups != 2 && rhs_groups != 4) ||
-        (rhs_groups > 1 && (sh.ds != 1 || sh.nr > 4 || ctx->batch)) || nrhs % (sh.nr * rhs_groups))
+        (rhs_groups > 1 && (sh.ds != 1 || sh.nr > 4 || ctx->batch || sh.wg > 1)) || nrhs % (sh.nr * rhs_groups))
         return set_error(ctx, HISQ_EINVAL, "hisq_tune_set_groups: groups must be 1, 2 or 4, with one thread per "
                                            "site, n_inner <= 4 and n_inner * groups dividing nrhs");
     it->second.rg = rhs_groups;
+    return HISQ_OK;
+}
+
+extern "C" int hisq_tune_set_block_groups(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int block_groups)
+{
+    if (!ctx) return HISQ_EINVAL;
+    auto it = ctx->tune.find(tune_key(prec_links, prec_vectors, nrhs));
+    if (it == ctx->tune.end()) return set_error(ctx, HISQ_EINVAL, "hisq_tune_set_block_groups: no shape for this key");
+    const DslashShape &sh = it->second;
+    if ((block_groups != 1 && block_groups != 2 && block_groups != 4) ||
+        (block_groups > 1 && (sh.ds != 1 || sh.nr > 4 || sh.rg != 1 || ctx->batch || sh.bs / block_groups < 32)) ||
+        nrhs % (sh.nr * block_groups))
+        return set_error(ctx, HISQ_EINVAL, "hisq_tune_set_block_groups: groups must be 1, 2 or 4, with one thread per "
+                                           "site, n_inner <= 4, no site groups, at least 32 threads per group "
+                                           "and n_inner * groups dividing nrhs");
+    it->second.wg = block_groups;
+    return HISQ_OK;
+}
+
+extern "C" int hisq_tune_get_block_groups(const hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs,
+                                          int *block_groups)
+{
+    if (!ctx || !block_groups) return HISQ_EINVAL;
+    auto it = ctx->tune.find(tune_key(prec_links, prec_vectors, nrhs));
+    if (it == ctx->tune.end()) return HISQ_EINVAL;
+    *block_groups = it->second.wg;
     return HISQ_OK;
 }
 

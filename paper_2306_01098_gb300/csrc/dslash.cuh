@@ -33,6 +33,7 @@ struct DslashArgs {
     int stream_links;      // link store larger than L2 can keep: load links evict-first
     int sm_count;          // SMs of the device (grid size)
     int bs;                // threads per block (64, 128 or 256; batches: kDslashBlock)
+    int wg;                // slices of a block over the same sites (DslashShape::wg; 0 or 1: none)
     uint32_t items;        // work items of the launch (set by the launcher)
     // batch of lattices (NULL for one lattice): device table, lattices, and from the host
     // copy of the table the tiles of all lattices / of the largest, per threads per site

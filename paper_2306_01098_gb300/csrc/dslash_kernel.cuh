@@ -121,8 +121,9 @@ __device__ __forceinline__ void vec_load(const char *base, uint32_t s, typename 
 // right-hand sides g NR .. g NR + NR - 1 from the given ones; their loads of the site's links
 // are the same addresses in the same instruction (one request), so a link is fetched once
 // for all NR RG right-hand sides with 1/RG of the accumulators per thread.
+// LL1: links allocate in L1 (right-hand-side groups of one block read the same links).
 template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool COH = false, bool PF = false, int RG = 1,
-          class DT = double>
+          class DT = double, bool LL1 = false>
 __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, const char *links, size_t slot_bytes,
                                             std::conditional_t<std::is_same<DT, FF>::value, float, double> sc0,
                                             std::conditional_t<std::is_same<DT, FF>::value, float, double> sc1,
@@ -196,7 +197,7 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
                     const uint32_t sn = neighbour(g, c, s, mu, k, wrap[h]);
                     const int lp = back ? 1 - a.p : a.p;
                     const char *slot = links + (size_t)((lp * 2 + type) * 4 + mu) * slot_bytes;
-                    load_link_words<LB>(slot, back ? sn : s, w[h], NR > 1 && a.stream_links != 0);
+                    load_link_words<LB, LL1>(slot, back ? sn : s, w[h], NR > 1 && a.stream_links != 0);
 #pragma unroll
                     for (int r = 0; r < NR; r++) vec_load<T, COH>(in + (size_t)r * a.rhs_bytes, sn, v[h][r]);
                 }
@@ -225,7 +226,7 @@ __device__ __forceinline__ void dslash_item(const DslashArgs &a, const Geom &g, 
                 const int lp = back ? 1 - a.p : a.p;
                 const char *slot = links + (size_t)((lp * 2 + type) * 4 + mu) * slot_bytes;
                 uint32_t w[LB / 4];
-                load_link_words<LB>(slot, back ? sn : s, w, NR > 1 && a.stream_links != 0);
+                load_link_words<LB, LL1>(slot, back ? sn : s, w, NR > 1 && a.stream_links != 0);
                 typename T::Link U;
                 TL::template unpack<NREAL>(w, U);
                 if constexpr (NREAL == 12) T::rebuild(U, (eta_neg(c, mu) != 0) ^ (mu == 3 && wrap));
@@ -308,9 +309,14 @@ __device__ __forceinline__ double dot_value(double x) { return x; }
 
 // BATCH: the lattices of a batch in one launch (NR = 1; right-hand side k is lattice k).
 // RG: groups of right-hand sides sharing a site's threads (dslash_item).
-template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH, int RG = 1>
+// WG > 1 (no epilogue, one thread per site, RG = 1): the block's threads form WG slices of
+// a.bs threads over the same sites, slice g taking the g-th of the block's WG groups of NR
+// right-hand sides; their link loads allocate in L1, so one L2 read of a link serves the
+// block's WG NR right-hand sides without the registers of WG NR accumulators per thread.
+template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH, int RG = 1, int WG = 1>
 __global__ void __launch_bounds__(kDslashMaxBlock) k_dslash(const DslashArgs a)
 {
+    static_assert(WG == 1 || (EPI == 0 && DS == 1 && RG == 1 && !BATCH), "block slices: plain Dslash, one thread per site");
     using T = Prec<PV>;
     using TL = Prec<PL>;
     static_assert(std::is_same<typename T::Link, typename TL::Link>::value, "link and vector arithmetic must agree");
@@ -389,15 +395,19 @@ __global__ void __launch_bounds__(kDslashMaxBlock) k_dslash(const DslashArgs a)
     } else {
         // gridDim.x is a multiple of the group count, so a block keeps one group of right-hand
         // sides while it strides over the work items (site tile, group)
-        const uint32_t ngroups = (uint32_t)(a.nrhs / (NR * RG));
-        const int rhs0 = (int)(blockIdx.x % ngroups) * NR * RG;
+        // (with WG slices, a block group is WG consecutive groups, slice g of the block taking
+        // the g-th; a.bs is then the threads of one slice)
+        const uint32_t ngroups = (uint32_t)(a.nrhs / (NR * RG * WG));
+        const uint32_t slice = WG > 1 ? threadIdx.x / (uint32_t)a.bs : 0u;
+        const uint32_t tid = WG > 1 ? threadIdx.x - slice * (uint32_t)a.bs : threadIdx.x;
+        const int rhs0 = (int)((blockIdx.x % ngroups) * WG + slice) * NR * RG;
         const size_t off = (size_t)rhs0 * a.rhs_bytes;
         const auto sc0 = [&] { if constexpr (FFK) return a.scale_f[0]; else return a.scale[0]; }();
         const auto sc1 = [&] { if constexpr (FFK) return a.scale_f[1]; else return a.scale[1]; }();
         for (uint32_t item = blockIdx.x; item < a.items; item += gridDim.x)
-            dslash_item<PL, PV, NREAL, NR, EPI, DS, false, false, RG, DTK>(
+            dslash_item<PL, PV, NREAL, NR, EPI, DS, false, false, RG, DTK, (WG > 1)>(
                 a, a.g, a.links, a.slot_bytes, sc0, sc1, a.in + off, a.out + off, EPI ? a.pv + off : nullptr,
-                EPI == 2 ? a.rv + off : nullptr, a.shift ? a.shift + rhs0 : nullptr, item / ngroups, dots);
+                EPI == 2 ? a.rv + off : nullptr, a.shift ? a.shift + rhs0 : nullptr, item / ngroups, dots, tid);
         if constexpr (EPI >= 1) {
             if (a.red.partials) { // uniform over the grid
                 if constexpr (RG == 1) {
@@ -422,7 +432,7 @@ __global__ void __launch_bounds__(kDslashMaxBlock) k_dslash(const DslashArgs a)
 // epilogue's reduction the grid holds at most as many blocks as are resident at once (a
 // multiple of the group count, from the occupancy of this instantiation) and blocks
 // stride over the items, so that there is one partial per block and right-hand side.
-template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH, int RG = 1>
+template <int PL, int PV, int NREAL, int NR, int EPI, int DS, bool BATCH, int RG = 1, int WG = 1>
 static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
 {
     DslashArgs a = a0;
@@ -433,8 +443,8 @@ static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
     const int bi = bs == 64 ? 0 : bs == 128 ? 1 : 2;
     if (occ[bi] < 0) {
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_dslash<PL, PV, NREAL, NR, EPI, DS, BATCH, RG>, bs, 0) !=
-                cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_dslash<PL, PV, NREAL, NR, EPI, DS, BATCH, RG, WG>, bs,
+                                                          0) != cudaSuccess ||
             o < 1)
             o = 1;
         occ[bi] = o;
@@ -450,8 +460,11 @@ static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
         k_dslash<PL, PV, NREAL, 1, EPI, DS, true><<<blocks, kDslashBlock, 0, st>>>(a);
         return cudaGetLastError();
     } else {
-        const size_t tiles = ((size_t)a.g.Vh * DS * RG + bs - 1) / bs;
-        const size_t ng = (size_t)(a.nrhs / (NR * RG));
+        const int ts = bs / WG; // threads over the sites of one tile (one slice of the block)
+        if (ts < 32) return cudaErrorInvalidValue;
+        a.bs = ts;
+        const size_t tiles = ((size_t)a.g.Vh * DS * RG + ts - 1) / ts;
+        const size_t ng = (size_t)(a.nrhs / (NR * RG * WG));
         const size_t items = tiles * ng;
         const size_t resident = std::max<size_t>(ng, (size_t)std::max(1, a.sm_count) * occ[bi] / ng * ng);
         const size_t blocks = a.red.partials ? std::min(items, resident) : items;
@@ -459,7 +472,7 @@ static cudaError_t launch_one(const DslashArgs &a0, cudaStream_t st)
         a.items = (uint32_t)items;
         a.red.nblocks = (int)(blocks / ng); // partials per right-hand side
         a.red.ntotal = (int)blocks;
-        k_dslash<PL, PV, NREAL, NR, EPI, DS, false, RG><<<(unsigned)blocks, bs, 0, st>>>(a);
+        k_dslash<PL, PV, NREAL, NR, EPI, DS, false, RG, WG><<<(unsigned)blocks, bs, 0, st>>>(a);
         return cudaGetLastError();
     }
 }
@@ -473,6 +486,21 @@ static cudaError_t launch_nr(const DslashArgs &a, int nr, int rg, cudaStream_t s
         return launch_one<PL, PV, NREAL, 1, EPI, DS, true>(a, st);
     }
     if (a.zt && !a.g.zt_ok) return cudaErrorInvalidValue;
+    if (a.wg > 1) { // slices of a block over the same sites: plain Dslash, one thread per site
+        if constexpr (EPI == 0 && DS == 1) {
+            if (rg == 1 && a.nrhs % (nr * a.wg) == 0) {
+                switch (a.wg * 16 + nr) {
+                case 2 * 16 + 1: return launch_one<PL, PV, NREAL, 1, 0, 1, false, 1, 2>(a, st);
+                case 2 * 16 + 2: return launch_one<PL, PV, NREAL, 2, 0, 1, false, 1, 2>(a, st);
+                case 2 * 16 + 4: return launch_one<PL, PV, NREAL, 4, 0, 1, false, 1, 2>(a, st);
+                case 4 * 16 + 1: return launch_one<PL, PV, NREAL, 1, 0, 1, false, 1, 4>(a, st);
+                case 4 * 16 + 2: return launch_one<PL, PV, NREAL, 2, 0, 1, false, 1, 4>(a, st);
+                case 4 * 16 + 4: return launch_one<PL, PV, NREAL, 4, 0, 1, false, 1, 4>(a, st);
+                }
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
     if (rg != 1) { // groups of right-hand sides on one site's threads: one thread per site only
         if constexpr (DS == 1) {
             switch (rg * 16 + nr) {

@@ -196,6 +196,8 @@ struct DslashShape {
     int order = 0; // 0: sites in storage order (t slowest); 1: z and t interchanged in launch order
     int bs = 128;  // threads per block (sites per block = bs / (ds rg))
     int rg = 1;    // groups of right-hand sides sharing one site's threads (ds = 1 only)
+    int wg = 1;    // groups of right-hand sides in one block, one slice of threads each, over the
+                   // same sites (links shared through L1; plain Dslash, ds = 1, rg = 1 only)
 };
 
 // key of a Dslash shape in the context's tuning table: link precision, vector precision and

@@ -43,17 +43,19 @@ def hbm_peak():
 
 
 def shapes(prec, nrhs, zt_ok=True):
-    """Every (n_inner, threads per site, site order, threads per block, right-hand-side groups)
-    launch shape the autotuner considers."""
+    """Every (n_inner, threads per site, site order, threads per block, right-hand-side groups
+    per site, right-hand-side groups per block) launch shape the autotuner considers."""
     cap = 4 if prec in ("f64", "f64x") else 8
     out = []
     for order in ((0, 1) if zt_ok else (0,)):
         nr = 1
         while nr <= cap:
             if nrhs % nr == 0:
-                out.extend((nr, ds, order, bs, 1) for ds in (1, 2, 4) for bs in (64, 128, 256))
-                out.extend((nr, 1, order, bs, rg) for rg in (2, 4) for bs in (64, 128, 256)
+                out.extend((nr, ds, order, bs, 1, 1) for ds in (1, 2, 4) for bs in (64, 128, 256))
+                out.extend((nr, 1, order, bs, rg, 1) for rg in (2, 4) for bs in (64, 128, 256)
                            if nr <= 4 and nrhs % (nr * rg) == 0)
+                out.extend((nr, 1, order, bs, 1, wg) for wg in (2, 4) for bs in (64, 128, 256)
+                           if nr <= 4 and nrhs % (nr * wg) == 0 and bs // wg >= 32)
             nr *= 2
     return out
 
@@ -85,6 +87,8 @@ def measure(dims=(64, 64, 64, 16), precs=("f64", "f64x", "f32", "f16"), nrhs_lis
                         ctx.tune_set_block(p, p, nrhs, sh[3])
                     if len(sh) > 4:
                         ctx.tune_set_groups(p, p, nrhs, sh[4])
+                    if len(sh) > 5:
+                        ctx.tune_set_block_groups(p, p, nrhs, sh[5])
                 for _ in range(3):
                     ctx.dslash_field(0, fi, fo)
                 torch.cuda.synchronize()
@@ -107,7 +111,8 @@ def measure(dims=(64, 64, 64, 16), precs=("f64", "f64x", "f32", "f16"), nrhs_lis
                 used = ctx.tune_get(p, p, nrhs)
                 if used is not None:
                     row["shape"] = {"n_inner": used[0], "threads_per_site": used[1], "site_order": used[2],
-                                    "threads_per_block": used[3], "rhs_groups": used[4], "autotuned": sh is None}
+                                    "threads_per_block": used[3], "rhs_groups": used[4],
+                                    "block_groups": ctx.tune_get_block_groups(p, p, nrhs), "autotuned": sh is None}
                 out.append(row)
             fi.close()
             fo.close()
@@ -123,7 +128,8 @@ def main():
     ap.add_argument("--comp", type=int, default=18)
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--shape", default=None,
-                    help="n_inner,threads_per_site,site_order[,threads_per_block[,rhs_groups]] instead of the autotuner")
+                    help="n_inner,threads_per_site,site_order[,threads_per_block[,rhs_groups[,block_groups]]] "
+                         "instead of the autotuner")
     ap.add_argument("--sweep", action="store_true", help="time every launch shape")
     ap.add_argument("--peaks", action="store_true",
                     help="print the measured FMA, L2/HBM, launch and grid-barrier roofs (hisq_measure_peaks)")

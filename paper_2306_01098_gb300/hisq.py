@@ -104,6 +104,8 @@ _SIGS = {
     "hisq_tune_set_block": (_I, [_P, _I, _I, _I, _I]),
     "hisq_tune_set_groups": (_I, [_P, _I, _I, _I, _I]),
     "hisq_tune_get": (_I, [_P, _I, _I, _I, ctypes.POINTER(_I)]),
+    "hisq_tune_set_block_groups": (_I, [_P, _I, _I, _I, _I]),
+    "hisq_tune_get_block_groups": (_I, [_P, _I, _I, _I, ctypes.POINTER(_I)]),
     "hisq_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
     "hisq_cg": (_I, [_P, _D, _P, _P, _I, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
     "hisq_multishift_cg": (_I, [_P, _D, _I, _P, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(Stats), _P]),
@@ -262,6 +264,15 @@ class Context:
 
     def tune_set_groups(self, prec_links, prec_vectors, nrhs, rhs_groups):
         return self.check(lib().hisq_tune_set_groups(self.h, prec_links, prec_vectors, nrhs, rhs_groups))
+
+    def tune_set_block_groups(self, prec_links, prec_vectors, nrhs, block_groups):
+        return self.check(lib().hisq_tune_set_block_groups(self.h, prec_links, prec_vectors, nrhs, block_groups))
+
+    def tune_get_block_groups(self, prec_links, prec_vectors, nrhs):
+        """Groups of right-hand sides per block stored for the key, or None."""
+        g = ctypes.c_int(0)
+        rc = lib().hisq_tune_get_block_groups(self.h, prec_links, prec_vectors, nrhs, ctypes.byref(g))
+        return g.value if rc == OK else None
 
     def tune_get(self, prec_links, prec_vectors, nrhs):
         """(n_inner, threads_per_site, site_order, threads_per_block, rhs_groups) stored for the

@@ -118,6 +118,55 @@ def test_dslash_multi_rhs(nrhs, prec):
             assert field_rel(got[r], want[r]) <= 2e-6
 
 
+@pytest.mark.parametrize("dims,order", [((6, 4, 8, 10), 0), ((10, 4, 6, 4), 0), ((8, 8, 8, 4), 1)])
+@pytest.mark.parametrize("prec", [hisq.F64, hisq.F32, hisq.F16])
+def test_dslash_block_groups(dims, order, prec):
+    # groups of right-hand sides per block (slices of a block over the same sites, links
+    # through L1): every slice count and block size gives the oracle's operator, and exactly
+    # the result of one group per block (the per-site arithmetic is the same); half volumes
+    # 960 and 480 leave ragged last tiles, 8x8x8x4 runs the z-t interchanged site order
+    nrhs = 8
+    ctx, fat, lng = setup(dims)
+    x = fields.gaussian_source(dims, 171, nrhs)
+    want = oracle.dslash(dims, fat, lng, x, 1)
+    pv = hisq.F32 if prec == hisq.F16 else prec
+    tol = {hisq.F32: 2e-6, hisq.F16: 3e-3}.get(prec)
+    for nr in (1, 2, 4):
+        for bs in (64, 128, 256):
+            ref = None
+            for wg in (1, 2, 4):
+                if bs // wg < 32 or nrhs % (nr * wg):
+                    continue
+                ctx.tune_set(prec, pv, nrhs, nr, 1, order)
+                ctx.tune_set_block(prec, pv, nrhs, bs)
+                ctx.tune_set_block_groups(prec, pv, nrhs, wg)
+                assert ctx.tune_get_block_groups(prec, pv, nrhs) == wg
+                assert ctx.tune_get(prec, pv, nrhs)[2] == order
+                out = torch.full_like(x, float("nan")).cuda()
+                ctx.dslash(1, x.cuda(), out, prec=prec)
+                got = out.cpu().numpy()
+                for r in range(nrhs):
+                    if tol is None:
+                        assert site_rel(got[r], want[r]) <= 1e-13, (nr, bs, wg, r)
+                    else:
+                        assert field_rel(got[r], want[r]) <= tol, (nr, bs, wg, r)
+                if ref is None:
+                    ref = got
+                else:
+                    assert np.array_equal(got, ref), (nr, bs, wg)
+    # shapes the block groups do not combine with are refused
+    ctx.tune_set(prec, pv, nrhs, 1, 2, order)
+    with pytest.raises(hisq.HisqError):
+        ctx.tune_set_block_groups(prec, pv, nrhs, 2)
+    ctx.tune_set(prec, pv, nrhs, 2, 1, order)
+    ctx.tune_set_block(prec, pv, nrhs, 64)
+    with pytest.raises(hisq.HisqError):
+        ctx.tune_set_block_groups(prec, pv, nrhs, 4)   # 16 threads per slice
+    ctx.tune_set(prec, pv, nrhs, 4, 1, order)
+    with pytest.raises(hisq.HisqError):
+        ctx.tune_set_block_groups(prec, pv, nrhs, 4)   # 4 x 4 right-hand sides do not divide 8
+
+
 @pytest.mark.parametrize("prec", [hisq.F64, hisq.F64X, hisq.F32, hisq.F16, hisq.BF16])
 def test_dslash_every_launch_shape(prec):
     # every (right-hand sides per thread, threads per site, right-hand-side groups per site,
