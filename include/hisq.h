@@ -177,8 +177,9 @@ int hisq_mdagm_noalloc(hisq_ctx *ctx, double m, const double *in, double *out, i
  * Nx/2 * Ny sites, is a multiple of 32), -1 the size-based default.  Vector precision equals
  * the link precision, or is HISQ_F32 with 16-bit links.  Results do not depend on the shape
  * beyond the rounding order of the reductions.  Returns HISQ_EINVAL for any other value.
- * The autotuner also searches 64, 128 and 256 threads per block (hisq_tune_set_block) and
- * groups of right-hand sides sharing a site (hisq_tune_set_groups). */
+ * The autotuner also searches 64, 128 and 256 threads per block (hisq_tune_set_block),
+ * groups of right-hand sides sharing a site (hisq_tune_set_groups) and groups of right-hand
+ * sides per block (hisq_tune_set_block_groups). */
 int hisq_tune_set(hisq_ctx *ctx, int prec_links, int prec_vectors, int nrhs, int n_inner, int threads_per_site,
                   int site_order);
 /* Threads per block (64, 128 or 256; sites per block = threads / threads_per_site) of the shape
